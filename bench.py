@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the Graph Normalization hot path on GB300.
+
+Workload: the 1M-edge plain-GN configuration -- a unit-disk graph (n = 200,000, |E| ~ 1.0M,
+w ~ lognormal(0,1), random labels) and a Barabasi-Albert graph (n = 200,000, m = 5,
+|E| ~ 1.0M, w ~ U[1,100]), synthetic and seeded.  One step runs both graphs through the
+whole path: gn_run from x0 = 1/(deg+1) with the paper's gamma pursuit until the state is
+binary (<= 2000 iterations, tol 1e-7, check every 10 iterations), then gn_extract_is
+(rounding, exact independence and maximality checks, member list, FP64 W(S)).
+
+Metric: GN edge-updates/s = sum over graphs of nnz x iterations / step time (nnz = directed
+CSR entries), plus time-to-binary-MIS per graph.  `value` has the graphs resident in HBM;
+`e2e` times the same step through the C ABI from host buffers (gn_create .. gn_destroy,
+host<->device copies included).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gn|reference]
+
+N > 1 runs under torchrun as independent replicas (one workload per rank, seeds offset by
+rank; no collective on the data path).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GN edge-updates/s & time-to-binary-MIS vs plain GN at ≤0.1% objective gap"
+UNIT = "edge-updates/s"
+MAX_ITERS = 2000
+TOL = 1e-7
+CHECK_EVERY = 10
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gn", choices=["gn", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(rank: int):
+    from paper_2605_05330_gb300 import inputs
+    base = inputs.SEED_BASE + 1000 * rank
+    return [inputs.workload_udg_1m(seed=base), inputs.workload_ba_1m(seed=base + 1)]
+
+
+def bytes_per_iter(inst) -> int:
+    """Algorithmic bytes of one iteration: col_idx (4 nnz) + row_ptr (4 (n+1)) + y read,
+    v read, y written (4 n each)."""
+    return 4 * inst.nnz + 4 * (inst.n + 1) + 12 * inst.n
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the persistent kernel from the committed ncu summary, when it
+    was taken on the current kernel source (else null)."""
+    p = os.path.join(ROOT, "profiles", "gn_persistent_traffic.json")
+    src = os.path.join(ROOT, "paper_2605_05330_gb300", "csrc", "gn_iterate.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("source_sha256") != h:
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+def cpu_sample(insts, iters_each=150):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample: the first
+    `iters_each` iterations of each graph of the workload."""
+    import oracle
+    t = time.perf_counter()
+    units = 0
+    for g in insts:
+        p = oracle.params(check_every=CHECK_EVERY)
+        x, info = oracle.run(g.row_ptr, g.col_idx, g.w, max_iters=iters_each, tol=TOL, p=p)
+        units += g.nnz * info["iters"]
+    dt = time.perf_counter() - t
+    return units / dt, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    insts = make_workload(0)
+    from paper_2605_05330_gb300 import inputs  # noqa: F401
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, dt = cpu_sample(insts, iters_each=60)
+        if s >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = 1000 * statistics.mean(dt for _, dt in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "udg_n200000_e1M+ba_n200000_m5", "sample": "first 60 iterations of each graph"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first 60 GN iterations of each 1M-edge graph, FP64, one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_2605_05330_gb300 import build
+    build.build()
+    from paper_2605_05330_gb300 import gn
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    insts = make_workload(rank)
+    dev = torch.device("cuda", local)
+    graphs = []
+    for inst in insts:
+        g = gn.Graph(torch.from_numpy(inst.row_ptr).to(dev), torch.from_numpy(inst.col_idx).to(dev),
+                     torch.from_numpy(inst.w).to(dev))
+        graphs.append(g)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(record):
+        for g, inst in zip(graphs, insts):
+            x, info = g.run(max_iters=MAX_ITERS, tol=TOL)
+            st, mask, members, cnt, W = g.extract_is()
+            if st not in ("OK", "WARN_NOT_MAXIMAL"):
+                raise RuntimeError(f"extraction failed on {inst.name}: {st}")
+            if record is not None:
+                record.append((inst, info, cnt, W))
+
+    for _ in range(args.warmup):
+        step(None)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    records = []
+    times = []
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = int(gn.lib().gn_kernel_launches())
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(records)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = int(gn.lib().gn_kernel_launches()) - launches0
+
+    ms_step = statistics.mean(times)
+    units_step = sum(inst.nnz * info["iters"] for inst, info, _, _ in records) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        u = torch.tensor([units_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units_step = float(u.item())
+    value = units_step / (ms_step / 1000.0)
+
+    # roofline of the dominant kernel (the persistent iteration kernel): algorithmic bytes per
+    # launch over its CUDA-event duration, averaged over the timed launches
+    alg_bytes = sum(bytes_per_iter(inst) * info["iters"] for inst, info, _, _ in records)
+    kern_ms = sum(info["device_ms"] for _, info, _, _ in records)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kern_ms / 1000.0) / 1e9
+    per_graph = {}
+    for inst, info, cnt, W in records:
+        d = per_graph.setdefault(inst.name, {"n": inst.n, "nnz": inst.nnz, "iters": [], "kernel_ms": [],
+                                             "mis_size": cnt, "mis_weight": W, "status": info["status"]})
+        d["iters"].append(info["iters"])
+        d["kernel_ms"].append(info["device_ms"])
+    for d in per_graph.values():
+        d["iters"] = int(statistics.median(d["iters"]))
+        d["time_to_binary_ms"] = statistics.median(d.pop("kernel_ms"))
+        d["edge_updates_per_s"] = d["nnz"] * d["iters"] / (d["time_to_binary_ms"] / 1000.0)
+
+    e2e = None
+    if not args.no_e2e:
+        hosts = []
+        for inst in insts:
+            rp = torch.from_numpy(inst.row_ptr).pin_memory()
+            ci = torch.from_numpy(inst.col_idx).pin_memory()
+            w = torch.from_numpy(inst.w).pin_memory()
+            xo = torch.empty(inst.n, dtype=torch.float32).pin_memory()
+            mk = torch.empty(inst.n, dtype=torch.uint8).pin_memory()
+            mb = torch.empty(inst.n, dtype=torch.int32).pin_memory()
+            hosts.append((inst, rp, ci, w, xo, mk, mb))
+        L = gn.lib()
+        P = ctypes.c_void_p
+
+        def e2e_step():
+            units = 0
+            h2d = d2h = 0
+            for inst, rp, ci, w, xo, mk, mb in hosts:
+                h = P()
+                st = L.gn_create(ctypes.byref(h), inst.n, P(rp.data_ptr()), P(ci.data_ptr()), P(w.data_ptr()),
+                                 gn.HOST, 0, P(stream.cuda_stream))
+                assert st == 0, L.gn_last_error()
+                info = gn.RunInfo()
+                p = gn.default_params()
+                st = L.gn_run(h, None, MAX_ITERS, TOL, ctypes.byref(p), 0, P(xo.data_ptr()), ctypes.byref(info))
+                assert st >= 0, L.gn_last_error()
+                cnt = ctypes.c_int32(0)
+                wt = ctypes.c_double(0)
+                st = L.gn_extract_is(h, None, P(mk.data_ptr()), P(mb.data_ptr()),
+                                     ctypes.cast(ctypes.pointer(cnt), P), ctypes.cast(ctypes.pointer(wt), P))
+                assert st >= 0, L.gn_last_error()
+                L.gn_destroy(h)
+                units += inst.nnz * info.iters
+                h2d += 4 * (inst.n + 1) + 4 * inst.nnz + 4 * inst.n
+                d2h += 4 * inst.n + inst.n + 4 * cnt.value + 8
+            return units, h2d, d2h
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            units, h2d, d2h = e2e_step()
+            torch.cuda.synchronize()
+            tt.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(tt)
+        e2e_units = units
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+            u = torch.tensor([float(units)], device=dev, dtype=torch.float64)
+            dist.all_reduce(u, op=dist.ReduceOp.SUM)
+            e2e_units = float(u.item())
+        e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1000 * e2e_s}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt = cpu_sample(insts)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first 150 GN iterations of each 1M-edge graph, FP64, one thread ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "udg_n200000_e1M+ba_n200000_m5", "parallelism": "replicas" if world > 1 else "single",
+                       "graphs": per_graph, "max_iters": MAX_ITERS, "tol": TOL, "check_every": CHECK_EVERY,
+                       "gamma": "pursuit 0.9->1.5 over 1000", "l2": "flushed between timed steps (256 MB write)",
+                       "reductions": "fp64"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(),
+                         "kernel": "k_gn_persistent", "peak_kind": peak_kind,
+                         "bytes_per_iter": "4 nnz + 4 (n+1) + 12 n"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    for g in graphs:
+        g.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * gn.h -- C ABI of the GB300 Graph Normalization library (libgn.so).
+ *
+ * Graph Normalization (arXiv 2605.05330) iterates the weighted regularised map
+ * (Def. WRGN, Sec. 2)
+ *
+ *     x_i  <-  x_i / ( x_i + gamma * sum_{j in N(i)} (v_j / v_i) x_j ),   v = sqrt(w),
+ *
+ * on a sparse conflict graph until the state binarises into the indicator of a
+ * maximal independent set (Thm. 3).  The library runs the iteration on the GPU in
+ * the weighted state y = v (.) x (App. B: y_i <- v_i y_i / ((I + gamma A) y)_i), in
+ * FP32, with FP64 reductions.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status codes: 0 = success, > 0 = warning (results are written), < 0 = error
+ *   (outputs are unspecified).  No call throws, traps the GPU or aborts the process.
+ *   gn_last_error() returns a message for the last non-zero status of this thread.
+ * - Memory side: every pointer argument after gn_create lives on the side selected by
+ *   the handle's I/O mode (GN_HOST or GN_DEVICE; set at gn_create, changed with
+ *   gn_set_io).  Device pointers must belong to the handle's device.
+ * - Streams: all device work of a handle is issued on its stream (gn_create's
+ *   `stream`, a cudaStream_t, NULL = legacy default stream).  Calls that return
+ *   results to the host, or a status that depends on device results, synchronise
+ *   that stream before returning.
+ * - Ownership: gn_create copies the caller's arrays into handle-owned device memory;
+ *   the caller keeps ownership of every buffer it passes to any call.
+ * - Vertex ids are 0-based in the caller's order.  An internal reordering (params
+ *   `reorder`) is undone on every output.
+ * - A handle is not thread-safe; distinct handles may be used concurrently.
+ */
+#ifndef GN_H_
+#define GN_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GN_OK = 0,
+  GN_WARN_NOT_CONVERGED = 1,    /* max_iters reached before the stop test fired */
+  GN_WARN_NOT_BINARY = 2,       /* residual below tol on a state that is not binary */
+  GN_WARN_NOT_MAXIMAL = 3,      /* extracted set is independent but not maximal */
+  GN_ERR_ARG = -1,              /* bad argument or malformed CSR encoding */
+  GN_ERR_NOT_SIMPLE = -2,       /* self-loop, duplicate/unsorted row, or asymmetric A */
+  GN_ERR_WEIGHT = -3,           /* a weight is <= 0 or not finite */
+  GN_ERR_NOT_NORMALIZABLE = -4, /* x0 < 0, not finite, or (A + I) x0 has a zero entry */
+  GN_ERR_CUDA = -5,             /* a CUDA runtime call failed */
+  GN_ERR_TIMEOUT = -6,          /* a device-side wait hit its limit; kernel returned early */
+  GN_ERR_NOT_INDEPENDENT = -7,  /* the rounded set has an edge inside */
+  GN_ERR_NO_RECORD = -8,        /* gn_backward without a recorded forward run */
+  GN_ERR_TOO_LARGE = -9         /* size beyond a documented limit */
+} gn_status;
+
+#define GN_HOST 0
+#define GN_DEVICE 1
+
+#define GN_GAMMA_PURSUIT 0      /* gamma_k = t gamma1 + (1-t) gamma0, t = min(k,T-1)/(T-1) (Sec. 6) */
+#define GN_GAMMA_FIXED 1        /* gamma_k = gamma1 */
+
+#define GN_REORDER_NONE 0
+#define GN_REORDER_RCM 1        /* reverse Cuthill-McKee: locality of neighbour gathers */
+#define GN_REORDER_DEGREE 2     /* descending degree */
+
+#define GN_KERNEL_AUTO 0
+#define GN_KERNEL_PERSISTENT 1  /* multi-CTA persistent kernel with a bounded grid barrier */
+#define GN_KERNEL_CTA 2         /* whole graph in one CTA's shared memory */
+
+typedef struct {
+  int gamma_mode;       /* GN_GAMMA_PURSUIT (default) or GN_GAMMA_FIXED */
+  double gamma0;        /* pursuit start (default 0.9, Sec. 6) */
+  double gamma1;        /* pursuit end / fixed value (default 1.5, Sec. 6) */
+  int ramp_iters;       /* pursuit length T (default 1000, Sec. 6) */
+  int check_every;      /* stop-test cadence c >= 1 (default 10) */
+  double theta_bin;     /* binarity threshold theta (default 1e-4) */
+  int kernel;           /* GN_KERNEL_* (default AUTO) */
+  int record;           /* 1: keep sqrt(T) checkpoints of this run for gn_backward */
+  long long spin_limit; /* device wait limit in polls (0 = default 1<<22) */
+  int debug_unreachable_barrier; /* test hook: make the first grid barrier unreachable so
+                                    that every CTA hits spin_limit; must be 0 in use */
+  int resume;           /* 1: continue from the full-precision state the last gn_run left on the
+                           handle (x0 ignored); with start_iter = that run's end this reproduces
+                           an uninterrupted run bit for bit */
+} gn_params;
+
+typedef struct {
+  int iters;            /* iterations performed by this call */
+  int converged;        /* 1 if the stop test fired */
+  int binary;           /* 1 if every x_i <= theta or >= 1 - theta at the last check */
+  int status;           /* the gn_status returned */
+  double resid_inf;     /* max_i |x_i^{k+1} - x_i^k| of the last step */
+  double resid_l1;      /* sum_i |x_i^{k+1} - x_i^k| of the last step (FP64) */
+  double objective;     /* sum_i w_i x_i of the returned state (FP64), Thm. 4 */
+  double energy;        /* E~(y) = 1/2 y^T (I + gamma A) y - v^T y (Sec. 3) of the state that
+                           entered the last step, at that step's gamma (FP64) */
+  long long safe_div_hits; /* steps where (B y)_i <= 1e-9 set x_i = 1/2 (appendix module) */
+  float device_ms;      /* device time of the iteration kernel(s) */
+  int kernel;           /* kernel that ran (GN_KERNEL_PERSISTENT or GN_KERNEL_CTA) */
+} gn_run_info;
+
+typedef struct gn_graph gn_graph;
+
+/* Fills *p with the defaults listed in gn_params. */
+void gn_default_params(gn_params* p);
+
+/*
+ * gn_create -- a1 of the path: validate, upload and prepare a graph.  Sec. 2: A must be
+ * the adjacency matrix of a simple undirected graph (symmetric, zero diagonal); Def. WRGN:
+ * w in R_{++}^n, v = sqrt(w).
+ *   n        number of vertices, 0 <= n < 2^31
+ *   row_ptr  int32[n+1], row_ptr[0] = 0, non-decreasing; nnz = row_ptr[n] directed entries
+ *   col_idx  int32[nnz]; row i lists N(i) strictly increasing, no i itself; j in N(i)
+ *            iff i in N(j)
+ *   w        float32[n], finite and > 0
+ *   mem      GN_HOST or GN_DEVICE: where row_ptr/col_idx/w live; becomes the I/O mode
+ *   reorder  GN_REORDER_*: internal vertex order (undone on output)
+ *   stream   cudaStream_t for all device work of the handle (NULL = default stream)
+ * On success *g owns device copies of everything.  Errors: GN_ERR_ARG, GN_ERR_NOT_SIMPLE,
+ * GN_ERR_WEIGHT, GN_ERR_CUDA (no handle is returned on error).
+ */
+gn_status gn_create(gn_graph** g, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                    const float* w, int mem, int reorder, void* stream);
+
+/* Releases every resource of the handle (NULL is a no-op). */
+void gn_destroy(gn_graph* g);
+
+/* Changes the memory side (GN_HOST / GN_DEVICE) of the pointers of later calls. */
+gn_status gn_set_io(gn_graph* g, int mem);
+
+/* Graph size queries. */
+int32_t gn_num_vertices(const gn_graph* g);
+int64_t gn_num_entries(const gn_graph* g);
+
+/*
+ * gn_run -- a2..a7 of the path: iterated WRGN (Def. WRGN, Def. IGN) with the gamma
+ * schedule of Sec. 6, from x0, until the stop test fires or the iteration index reaches
+ * max_iters; then x_out = clamp(x, 0, 1) (appendix module).
+ *   x0          float32[n] start (finite, >= 0, (A + I) x0 > 0 -- Def. 1), or NULL for
+ *               x0_i = 1/(deg_i + 1)
+ *   max_iters   absolute bound: iterations k = start_iter .. max_iters-1 run at most
+ *   tol         residual stop: max_i |x_i^{k+1} - x_i^k| <= tol (negative disables)
+ *   p           parameters (NULL = defaults)
+ *   start_iter  absolute index of the first iteration (gamma_k depends on k); a run resumed
+ *               with start_iter = K from a saved FP32 state x^K follows the uninterrupted one
+ *               to within the FP32 rounding of x^K (params.resume continues bit for bit)
+ *   x_out       float32[n] result (may alias x0); NULL leaves the state on the device only
+ *   info        optional run summary
+ * Stop test (after step k when (k+1) % check_every == 0 or k+1 == max_iters): every
+ * x_i <= theta or >= 1-theta and gamma_k (1-theta) > theta (then the rounded set is
+ * independent), or the residual test.  One launch of the persistent kernel runs all
+ * iterations.  Returns GN_OK (binary), GN_WARN_NOT_BINARY, GN_WARN_NOT_CONVERGED, or an
+ * error (GN_ERR_ARG, GN_ERR_NOT_NORMALIZABLE, GN_ERR_TIMEOUT, GN_ERR_CUDA).
+ */
+gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double tol, const gn_params* p,
+                 int start_iter, float* x_out, gn_run_info* info);
+
+/*
+ * gn_extract_is -- a8 of the path (Sec. 2 independent sets; Sec. 6 "valid MIS after
+ * rounding"): S = {i : x_i > 1/2}; exact independence check over every edge; maximality
+ * check; |S|; W(S) = sum_{i in S} w_i in FP64.
+ *   x        float32[n] state (NULL = the state left by the last gn_run)
+ *   mask     uint8[n] output, 1 for members (may be NULL)
+ *   members  int32[n] output, member ids ascending (may be NULL)
+ *   count    |S| (may be NULL); weight W(S) (may be NULL)
+ * Returns GN_OK, GN_WARN_NOT_MAXIMAL, GN_ERR_NOT_INDEPENDENT (outputs still written), or an
+ * error.
+ */
+gn_status gn_extract_is(gn_graph* g, const float* x, uint8_t* mask, int32_t* members,
+                        int32_t* count, double* weight);
+
+/*
+ * gn_objective -- FP64 relaxed MWIS objective sum_i w_i x_i (Thm. 4) and the energy
+ * E~(y) = 1/2 y^T (I + gamma A) y - v^T y, y = v (.) x (Sec. 3), of a state x (NULL = the
+ * state left by the last gn_run).  Either output may be NULL.
+ */
+gn_status gn_objective(gn_graph* g, const float* x, double gamma, double* obj, double* energy);
+
+/*
+ * gn_backward -- reverse mode of the last recorded gn_run (params.record = 1, gamma pursuit
+ * or fixed, a fixed number of iterations: use tol < 0 and theta_bin < 0 so that the stop
+ * test never fires).  Derived from the step's Jacobian (Lemma 1 of App. F, general form):
+ * with s = (I + gamma A) y, the adjoint of y' = v (.) y / s is
+ *   gbar_y = v (.) gbar' / s - (I + gamma A)(v (.) gbar' (.) y / s^2),
+ *   gbar_v += gbar' (.) y / s.
+ * Recomputation from sqrt(T) checkpoints.
+ *   dL_dxT  float32[n] gradient of the loss w.r.t. the returned x (before the clamp, which
+ *           is the identity on the iterates)
+ *   dL_dw   float32[n] output, gradient w.r.t. w (may be NULL)
+ *   dL_dx0  float32[n] output, gradient w.r.t. x0 (may be NULL)
+ * Safe-division hits have zero gradient.  Errors: GN_ERR_NO_RECORD, GN_ERR_ARG, GN_ERR_CUDA.
+ */
+gn_status gn_backward(gn_graph* g, const float* dL_dxT, float* dL_dw, float* dL_dx0);
+
+/* Number of CUDA kernels this library has launched in the process so far (all handles,
+ * all threads).  Lets a caller count the device work behind a sequence of calls. */
+int64_t gn_kernel_launches(void);
+
+/* Message of the last non-zero status returned on this thread ("" if none). */
+const char* gn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

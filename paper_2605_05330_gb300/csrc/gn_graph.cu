@@ -1,0 +1,382 @@
+// gn_graph.cu -- a1 of the path: gn_create / gn_destroy.  Uploads the CSR and weights,
+// validates them on the device (Sec. 2: simple undirected graph; Def. WRGN: w > 0),
+// computes v = sqrt(w), optionally reorders the vertices (RCM or by degree) for gather
+// locality, and partitions the rows across the persistent kernel's CTAs.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "gn_internal.cuh"
+
+namespace gn {
+
+static thread_local std::string t_last_error;
+static std::atomic<long long> g_launches{0};
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+gn_status fail(gn_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+gn_status cuda_fail(cudaError_t e, const char* what) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  return fail(GN_ERR_CUDA, buf);
+}
+
+// ------------------------------------------------------------------------------------------
+// validation kernels
+
+// rows: entries in range, strictly increasing (sorted, no duplicates), no self-loop
+__global__ void k_check_rows(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = 0;
+  int b = rp[i], e = rp[i + 1];
+  int prev = -1;
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j < 0 || j >= n) { f |= DEV_BAD_CSR; break; }
+    if (j == i || j <= prev) f |= DEV_NOT_SIMPLE;
+    prev = j;
+  }
+  if (f) atomicOr(flags, f);
+}
+
+// symmetry: for every entry (i, j), i appears in row j (binary search; rows are sorted)
+__global__ void k_check_symmetry(int n, int64_t nnz, const int32_t* __restrict__ rp,
+                                 const int32_t* __restrict__ ci, int* flags) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  // row of entry e: the last i with rp[i] <= e
+  int lo = 0, hi = n;  // invariant: rp[lo] <= e < rp[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if ((int64_t)rp[mid] <= e) lo = mid; else hi = mid;
+  }
+  int i = lo, j = ci[e];
+  int a = rp[j], b = rp[j + 1] - 1;
+  bool found = false;
+  while (a <= b) {
+    int m = (a + b) >> 1;
+    int c = ci[m];
+    if (c == i) { found = true; break; }
+    if (c < i) a = m + 1; else b = m - 1;
+  }
+  if (!found) atomicOr(flags, DEV_NOT_SIMPLE);
+}
+
+// weights: finite and positive; v = sqrt(w) (Def. WRGN), kept as a float pair v_hi + v_lo
+// (an FP64 square root split once), so that the map's weight ratios carry no FP32 bias
+__global__ void k_weights(int n, const float* __restrict__ w, float* __restrict__ v,
+                          float* __restrict__ vlo, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float wi = w[i];
+  if (!(wi > 0.0f) || !isfinite(wi)) {
+    atomicOr(flags, DEV_BAD_WEIGHT);
+    v[i] = 1.0f;
+    vlo[i] = 0.0f;
+    return;
+  }
+  dev::f2 p = dev::split_f64(sqrt((double)wi));
+  v[i] = p.hi;
+  vlo[i] = p.lo;
+}
+
+// permuted CSR: new row r is old row perm[r], neighbours renamed by iperm and re-sorted
+__global__ void k_permute_rows(int n, const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
+                               const int32_t* __restrict__ rp_old, const int32_t* __restrict__ ci_old,
+                               const int32_t* __restrict__ rp_new, int32_t* __restrict__ ci_new,
+                               const float* __restrict__ w_old, float* __restrict__ w_new) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int o = perm[r];
+  int b = rp_old[o], e = rp_old[o + 1];
+  int d = rp_new[r];
+  for (int k = b; k < e; ++k) ci_new[d + (k - b)] = iperm[ci_old[k]];
+  // insertion sort of the renamed row (rows are short; hubs pay once at create)
+  for (int a = d + 1; a < d + (e - b); ++a) {
+    int key = ci_new[a];
+    int c = a - 1;
+    while (c >= d && ci_new[c] > key) { ci_new[c + 1] = ci_new[c]; --c; }
+    ci_new[c + 1] = key;
+  }
+  w_new[r] = w_old[o];
+}
+
+static unsigned grid_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+// ------------------------------------------------------------------------------------------
+// host helpers
+
+gn_status upload_or_alias(gn_graph* g, const void* src, size_t bytes, const void** dev_ptr) {
+  if (g->io_mem == GN_DEVICE) {
+    *dev_ptr = src;
+    return GN_OK;
+  }
+  GN_CUDA(cudaMemcpyAsync(g->d_io, src, bytes, cudaMemcpyHostToDevice, g->stream));
+  *dev_ptr = g->d_io;
+  return GN_OK;
+}
+
+gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes) {
+  if (bytes == 0) return GN_OK;
+  GN_CUDA(cudaMemcpyAsync(dst, dev_src, bytes,
+                          g->io_mem == GN_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          g->stream));
+  return GN_OK;
+}
+
+// Reverse Cuthill-McKee over every component (BFS from a minimum-degree vertex, neighbours
+// visited in increasing degree), reversed.  perm[new] = old.
+static void rcm_order(int n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
+                      std::vector<int32_t>& perm) {
+  perm.clear();
+  perm.reserve(n);
+  std::vector<char> seen(n, 0);
+  std::vector<int32_t> byDeg(n);
+  std::iota(byDeg.begin(), byDeg.end(), 0);
+  std::stable_sort(byDeg.begin(), byDeg.end(),
+                   [&](int a, int b) { return rp[a + 1] - rp[a] < rp[b + 1] - rp[b]; });
+  std::vector<int32_t> nb;
+  for (int s : byDeg) {
+    if (seen[s]) continue;
+    size_t head = perm.size();
+    perm.push_back(s);
+    seen[s] = 1;
+    while (head < perm.size()) {
+      int u = perm[head++];
+      nb.clear();
+      for (int k = rp[u]; k < rp[u + 1]; ++k)
+        if (!seen[ci[k]]) { seen[ci[k]] = 1; nb.push_back(ci[k]); }
+      std::stable_sort(nb.begin(), nb.end(),
+                       [&](int a, int b) { return rp[a + 1] - rp[a] < rp[b + 1] - rp[b]; });
+      perm.insert(perm.end(), nb.begin(), nb.end());
+    }
+  }
+  std::reverse(perm.begin(), perm.end());
+}
+
+}  // namespace gn
+
+// ------------------------------------------------------------------------------------------
+// public ABI
+
+extern "C" void gn_default_params(gn_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof *p);
+  p->gamma_mode = GN_GAMMA_PURSUIT;
+  p->gamma0 = 0.9;
+  p->gamma1 = 1.5;
+  p->ramp_iters = 1000;
+  p->check_every = 10;
+  p->theta_bin = 1e-4;
+  p->kernel = GN_KERNEL_AUTO;
+  p->record = 0;
+  p->spin_limit = 0;
+  p->debug_unreachable_barrier = 0;
+  p->resume = 0;
+}
+
+extern "C" int64_t gn_kernel_launches(void) { return gn::g_launches.load(); }
+
+extern "C" const char* gn_last_error(void) { return gn::t_last_error.c_str(); }
+
+extern "C" int32_t gn_num_vertices(const gn_graph* g) { return g ? g->n : 0; }
+extern "C" int64_t gn_num_entries(const gn_graph* g) { return g ? g->nnz : 0; }
+
+extern "C" gn_status gn_set_io(gn_graph* g, int mem) {
+  if (!g || (mem != GN_HOST && mem != GN_DEVICE)) return gn::fail(GN_ERR_ARG, "gn_set_io: bad argument");
+  g->io_mem = mem;
+  return GN_OK;
+}
+
+void gn_free_record(gn_graph* g);  // gn_adjoint.cu
+
+extern "C" void gn_destroy(gn_graph* g) {
+  if (!g) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  gn_free_record(g);
+  void* dptrs[] = {g->d_row_ptr, g->d_col_idx, g->d_w, g->d_v, g->d_vlo, g->d_ylo, g->d_perm, g->d_iperm, g->d_part,
+                   g->d_y[0], g->d_y[1], g->d_x, g->d_tmp, g->d_bsum, g->d_io, g->d_partials, g->d_bar, g->d_info,
+                   g->d_flags, g->d_red, g->d_mask, g->d_mask_c, g->d_bcount, g->d_bws,
+                   g->d_members};
+  for (void* p : dptrs)
+    if (p) cudaFree(p);
+  if (g->h_info) cudaFreeHost(g->h_info);
+  if (g->h_flags) cudaFreeHost(g->h_flags);
+  if (g->h_red) cudaFreeHost(g->h_red);
+  if (g->ev0) cudaEventDestroy(g->ev0);
+  if (g->ev1) cudaEventDestroy(g->ev1);
+  delete g;
+  cudaSetDevice(cur);
+}
+
+namespace gn {
+gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp);  // gn_iterate.cu
+}
+
+extern "C" gn_status gn_create(gn_graph** out, int32_t n, const int32_t* row_ptr,
+                               const int32_t* col_idx, const float* w, int mem, int reorder,
+                               void* stream) {
+  using namespace gn;
+  if (!out) return fail(GN_ERR_ARG, "gn_create: out is NULL");
+  *out = nullptr;
+  if (n < 0 || !row_ptr || (!w && n > 0) || (mem != GN_HOST && mem != GN_DEVICE) ||
+      reorder < GN_REORDER_NONE || reorder > GN_REORDER_DEGREE)
+    return fail(GN_ERR_ARG, "gn_create: bad argument");
+
+  gn_graph* g = new gn_graph();
+  struct Guard {
+    gn_graph*& g;
+    ~Guard() { if (g) gn_destroy(g); }
+  } guard{g};
+  g->stream = (cudaStream_t)stream;
+  g->io_mem = mem;
+  g->n = n;
+  g->reorder = reorder;
+  GN_CUDA(cudaGetDevice(&g->device));
+  GN_CUDA(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+
+  // row_ptr on the host: structural checks and the partition need it
+  std::vector<int32_t> rp(n + 1);
+  if (mem == GN_HOST) {
+    memcpy(rp.data(), row_ptr, sizeof(int32_t) * (n + 1));
+  } else {
+    GN_CUDA(cudaMemcpyAsync(rp.data(), row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                            g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  if (rp[0] != 0) return fail(GN_ERR_ARG, "gn_create: row_ptr[0] != 0");
+  for (int i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return fail(GN_ERR_ARG, "gn_create: row_ptr decreases");
+  g->nnz = rp[n];
+  if (g->nnz > 0 && !col_idx) return fail(GN_ERR_ARG, "gn_create: col_idx is NULL");
+
+  size_t nb = sizeof(float) * std::max<int64_t>(n, 1);
+  GN_CUDA(cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * (n + 1)));
+  GN_CUDA(cudaMalloc(&g->d_col_idx, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1)));
+  GN_CUDA(cudaMalloc(&g->d_w, nb));
+  GN_CUDA(cudaMalloc(&g->d_v, nb));
+  GN_CUDA(cudaMalloc(&g->d_vlo, nb));
+  GN_CUDA(cudaMalloc(&g->d_ylo, nb));
+  GN_CUDA(cudaMalloc(&g->d_y[0], nb));
+  GN_CUDA(cudaMalloc(&g->d_y[1], nb));
+  GN_CUDA(cudaMalloc(&g->d_x, nb));
+  GN_CUDA(cudaMalloc(&g->d_tmp, nb));
+  GN_CUDA(cudaMalloc(&g->d_bsum, sizeof(double) * 4 * 1024));
+  GN_CUDA(cudaMalloc(&g->d_io, std::max<size_t>(nb, 8 * ((size_t)n + 8))));
+  GN_CUDA(cudaMalloc(&g->d_flags, sizeof(int) * 8));
+  GN_CUDA(cudaMalloc(&g->d_info, sizeof(DevInfo)));
+  GN_CUDA(cudaMalloc(&g->d_red, sizeof(double) * 8));
+  GN_CUDA(cudaMalloc(&g->d_bar, sizeof(unsigned) * 8));
+  GN_CUDA(cudaMalloc(&g->d_mask, std::max<int64_t>(n, 1)));
+  GN_CUDA(cudaMalloc(&g->d_mask_c, std::max<int64_t>(n, 1)));
+  GN_CUDA(cudaMalloc(&g->d_bcount, sizeof(int) * ((size_t)n / 256 + 2)));
+  GN_CUDA(cudaMalloc(&g->d_bws, sizeof(double) * ((size_t)n / 256 + 2)));
+  GN_CUDA(cudaMalloc(&g->d_members, sizeof(int32_t) * (std::max<int64_t>(n, 1) + 1)));
+  GN_CUDA(cudaMallocHost(&g->h_info, sizeof(DevInfo)));
+  GN_CUDA(cudaMallocHost(&g->h_flags, sizeof(int) * 8));
+  GN_CUDA(cudaMallocHost(&g->h_red, sizeof(double) * 8));
+  GN_CUDA(cudaEventCreate(&g->ev0));
+  GN_CUDA(cudaEventCreate(&g->ev1));
+
+  cudaMemcpyKind kind = mem == GN_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  GN_CUDA(cudaMemcpyAsync(g->d_row_ptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                          g->stream));
+  if (g->nnz > 0)
+    GN_CUDA(cudaMemcpyAsync(g->d_col_idx, col_idx, sizeof(int32_t) * g->nnz, kind, g->stream));
+  if (n > 0) GN_CUDA(cudaMemcpyAsync(g->d_w, w, sizeof(float) * n, kind, g->stream));
+
+  // device validation: range / order / self-loops first, symmetry only on in-range data
+  GN_CUDA(cudaMemsetAsync(g->d_flags, 0, sizeof(int) * 8, g->stream));
+  if (n > 0) {
+    k_check_rows<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_row_ptr, g->d_col_idx, g->d_flags);
+    GN_LAUNCHED();
+    k_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_w, g->d_v, g->d_vlo, g->d_flags);
+    GN_LAUNCHED();
+    GN_CUDA(cudaGetLastError());
+  }
+  GN_CUDA(cudaMemcpyAsync(g->h_flags, g->d_flags, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->h_flags[0] & DEV_BAD_CSR) return fail(GN_ERR_ARG, "gn_create: col_idx entry out of range");
+  if (g->nnz > 0) {
+    k_check_symmetry<<<grid_for(g->nnz, 256), 256, 0, g->stream>>>(n, g->nnz, g->d_row_ptr,
+                                                                  g->d_col_idx, g->d_flags);
+    GN_LAUNCHED();
+    GN_CUDA(cudaGetLastError());
+    GN_CUDA(cudaMemcpyAsync(g->h_flags, g->d_flags, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  if (g->h_flags[0] & DEV_NOT_SIMPLE)
+    return fail(GN_ERR_NOT_SIMPLE, "gn_create: graph is not simple (self-loop, unsorted or duplicate "
+                                   "row entries, or asymmetric adjacency)");
+  if (g->h_flags[0] & DEV_BAD_WEIGHT) return fail(GN_ERR_WEIGHT, "gn_create: weight <= 0 or not finite");
+
+  // optional locality reordering (internal; undone on every output)
+  if (reorder != GN_REORDER_NONE && n > 1) {
+    std::vector<int32_t> ci(g->nnz);
+    if (g->nnz > 0)
+      GN_CUDA(cudaMemcpyAsync(ci.data(), g->d_col_idx, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToHost,
+                              g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int32_t> perm;
+    if (reorder == GN_REORDER_RCM) {
+      rcm_order(n, rp, ci, perm);
+    } else {
+      perm.resize(n);
+      std::iota(perm.begin(), perm.end(), 0);
+      std::stable_sort(perm.begin(), perm.end(),
+                       [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+    }
+    std::vector<int32_t> iperm(n), rp2(n + 1);
+    for (int r = 0; r < n; ++r) iperm[perm[r]] = r;
+    rp2[0] = 0;
+    for (int r = 0; r < n; ++r) rp2[r + 1] = rp2[r] + (rp[perm[r] + 1] - rp[perm[r]]);
+    int32_t *d_rp2 = nullptr, *d_ci2 = nullptr;
+    float* d_w2 = nullptr;
+    GN_CUDA(cudaMalloc(&g->d_perm, sizeof(int32_t) * n));
+    GN_CUDA(cudaMalloc(&g->d_iperm, sizeof(int32_t) * n));
+    GN_CUDA(cudaMalloc(&d_rp2, sizeof(int32_t) * (n + 1)));
+    GN_CUDA(cudaMalloc(&d_ci2, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1)));
+    GN_CUDA(cudaMalloc(&d_w2, sizeof(float) * n));
+    GN_CUDA(cudaMemcpyAsync(g->d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
+    GN_CUDA(cudaMemcpyAsync(g->d_iperm, iperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
+    GN_CUDA(cudaMemcpyAsync(d_rp2, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, g->stream));
+    k_permute_rows<<<grid_for(n, 128), 128, 0, g->stream>>>(n, g->d_perm, g->d_iperm, g->d_row_ptr,
+                                                            g->d_col_idx, d_rp2, d_ci2, g->d_w, d_w2);
+    GN_LAUNCHED();
+    GN_CUDA(cudaGetLastError());
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+    cudaFree(g->d_row_ptr);
+    cudaFree(g->d_col_idx);
+    cudaFree(g->d_w);
+    g->d_row_ptr = d_rp2;
+    g->d_col_idx = d_ci2;
+    g->d_w = d_w2;
+    k_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_w, g->d_v, g->d_vlo, g->d_flags);
+    GN_LAUNCHED();
+    GN_CUDA(cudaGetLastError());
+    rp.swap(rp2);
+  }
+
+  gn_status st = configure_partition(g, rp);
+  if (st != GN_OK) return st;
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  *out = g;
+  g = nullptr;  // disarm the guard
+  return GN_OK;
+}

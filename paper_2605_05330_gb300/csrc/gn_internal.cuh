@@ -1,0 +1,267 @@
+// gn_internal.cuh -- shared internals of libgn.so (handle layout, error plumbing, device
+// helpers).  Not part of the public ABI (include/gn.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gn.h"
+
+namespace gn {
+
+// ------------------------------------------------------------------------------------------
+// error plumbing
+
+void set_error(const std::string& msg);
+gn_status fail(gn_status st, const std::string& msg);
+gn_status cuda_fail(cudaError_t e, const char* what);
+
+// every kernel launch of the library goes through GN_LAUNCHED() right after the <<<>>>
+void count_launch(int k = 1);
+#define GN_LAUNCHED() ::gn::count_launch()
+
+#define GN_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t e__ = (call);                                  \
+    if (e__ != cudaSuccess) return ::gn::cuda_fail(e__, #call); \
+  } while (0)
+
+// device-side status word (written by kernels, read once by the host)
+enum DevStatus : int {
+  DEV_OK = 0,
+  DEV_NOT_NORMALIZABLE = 1,
+  DEV_TIMEOUT = 2,
+  DEV_BAD_CSR = 4,
+  DEV_NOT_SIMPLE = 8,
+  DEV_BAD_WEIGHT = 16,
+};
+
+// per-CTA partial of a stop-test check (double-buffered by check parity)
+struct alignas(32) CheckPartial {
+  float rmax;           // max |x' - x|
+  unsigned nonbin;      // count of theta < x' < 1 - theta
+  double l1;            // sum |x' - x|
+  double obj;           // sum w x'
+  double energy;        // sum y (d/2 - v)  (E~ of the state entering the step)
+};
+
+// summary the iteration kernels leave on the device (one D2H copy per run)
+struct DevInfo {
+  int iters;
+  int converged;
+  int binary;
+  int final_parity;     // d_y[final_parity] holds the final weighted state
+  float resid_inf;
+  unsigned nonbin;
+  double resid_l1;
+  double objective;
+  double energy;
+  unsigned long long hits;
+  int status;
+  int pad;
+};
+
+struct RecordState;   // gn_adjoint.cu
+
+}  // namespace gn
+
+// ------------------------------------------------------------------------------------------
+// the handle
+
+struct gn_graph {
+  int device = 0;
+  int num_sms = 0;
+  int io_mem = GN_HOST;
+  cudaStream_t stream = nullptr;
+
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int reorder = GN_REORDER_NONE;
+
+  // graph (internal vertex order)
+  int32_t* d_row_ptr = nullptr;
+  int32_t* d_col_idx = nullptr;
+  float* d_w = nullptr;
+  float* d_v = nullptr;         // v = sqrt(w) rounded to FP32 (high part)
+  float* d_vlo = nullptr;       // sqrt(w) - v_hi (low part of the float pair)
+  int32_t* d_perm = nullptr;    // perm[internal] = caller id (nullptr if no reorder)
+  int32_t* d_iperm = nullptr;   // iperm[caller] = internal id
+
+  // persistent-kernel partition: CTA b owns internal rows [part[b], part[b+1])
+  int nblocks = 0;
+  int32_t* d_part = nullptr;
+  int max_rows = 0;             // max rows of one CTA
+  int64_t max_ents = 0;         // max CSR entries of one CTA
+  int group = 4;                // lanes per light row
+  int heavy = 128;              // rows with more entries go warp-per-row
+  bool csr_in_smem = false;
+  size_t smem_bytes = 0;
+  int threads = 1024;
+
+  // state and scratch (device)
+  float* d_y[2] = {nullptr, nullptr};
+  float* d_x = nullptr;         // last returned state (internal order, clamped)
+  float* d_ylo = nullptr;       // low parts of the vertices' own weighted states after a run
+  int state_parity = 0;         // d_y[state_parity] holds the high parts of that state
+  float* d_io = nullptr;        // staging for x0 / outputs (caller order)
+  float* d_tmp = nullptr;       // internal-order scratch state
+  double* d_bsum = nullptr;     // per-CTA FP64 partial sums of the small reductions
+  gn::CheckPartial* d_partials = nullptr;  // [2][nblocks]
+  unsigned* d_bar = nullptr;
+  gn::DevInfo* d_info = nullptr;
+  gn::DevInfo* h_info = nullptr;           // pinned
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;                  // pinned
+  double* d_red = nullptr;                 // small FP64 scratch for reductions
+  double* h_red = nullptr;                 // pinned
+  uint8_t* d_mask = nullptr;    // rounded set, internal order
+  uint8_t* d_mask_c = nullptr;  // rounded set, caller order
+  int* d_bcount = nullptr;      // per-CTA member counts / offsets (extraction)
+  double* d_bws = nullptr;      // per-CTA W(S) partials (extraction)
+  int32_t* d_members = nullptr;
+  bool has_state = false;
+
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  gn::RecordState* rec = nullptr;          // checkpoints for gn_backward
+};
+
+namespace gn {
+
+// implemented in gn_iterate.cu
+gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const gn_params& p,
+                         int parity0, DevInfo* out, float* ms, int* kernel_used);
+gn_status init_state(gn_graph* g, const float* x0_dev_caller_order);
+double host_gamma(const gn_params& p, int k);
+// implemented in gn_extract.cu
+gn_status state_stats(gn_graph* g, const float* x_int, double theta, double* obj, unsigned* nonbin);
+gn_status to_internal(gn_graph* g, const float* x_caller, const float** x_int);
+// implemented in gn_graph.cu
+gn_status upload_or_alias(gn_graph* g, const void* src, size_t bytes, const void** dev_ptr);
+gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes);
+
+}  // namespace gn
+
+// ------------------------------------------------------------------------------------------
+// device helpers
+
+namespace gn {
+namespace dev {
+
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_int(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Grid-wide barrier for a cooperative launch (every CTA co-resident).  The counter only
+// grows: the e-th barrier of the launch waits for nblocks * (e + 1) arrivals.  The wait is
+// bounded: after `spin_limit` polls (or when another CTA has already reported a failure)
+// the CTA records DEV_TIMEOUT and returns false, so the kernel can wind down instead of
+// hanging.  Fence-fence synchronisation (release fence before the arrival, acquire fence
+// after the observed count) orders every write before the barrier with every read after it.
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target, int* status,
+                                             long long spin_limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fence_acq_rel();
+    atomicAdd(counter, 1u);
+    int ok = 1;
+    long long spins = 0;
+    while (ld_relaxed(counter) < target) {
+      ++spins;
+      if ((spins & 255) == 0 && ld_relaxed_int(status) != 0) { ok = 0; break; }
+      if (spins > spin_limit) {
+        atomicOr(status, DEV_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    fence_acq_rel();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ unsigned warp_sum_u(unsigned v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- float-pair ("double-float") arithmetic on the FP32 pipes.  A value is hi + lo with
+// |lo| <= ulp(hi)/2; error-free transforms use round-to-nearest intrinsics so that the
+// compiler cannot contract or reorder them.
+struct f2 {
+  float hi, lo;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// (a_hi + a_lo) * (b_hi + b_lo), normalised
+__device__ __forceinline__ f2 mul_f2(f2 a, f2 b) {
+  f2 p = two_prod(a.hi, b.hi);
+  float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+  return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+}
+// a / b for float pairs (one IEEE division plus one correction step)
+__device__ __forceinline__ f2 div_f2(f2 a, f2 b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  f2 t = two_prod(q1, b.hi);
+  float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, t.hi), t.lo), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
+  float q2 = __fdiv_rn(r, b.hi);
+  return fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ f2 split_f64(double v) {
+  float hi = __double2float_rn(v);
+  return {hi, __double2float_rn(v - (double)hi)};
+}
+
+// gamma_k of Sec. 6 / the appendix module, in FP64 (then rounded once to FP32 by callers)
+__device__ __forceinline__ double gamma_at(int mode, double g0, double g1, int T, int k) {
+  if (mode == GN_GAMMA_FIXED || T <= 1) return g1;
+  int kk = k < T - 1 ? k : T - 1;
+  double t = __ddiv_rn((double)kk, (double)(T - 1));
+  return __dadd_rn(__dmul_rn(t, g1), __dmul_rn(__dsub_rn(1.0, t), g0));  // no contraction
+}
+
+}  // namespace dev
+}  // namespace gn

@@ -1,0 +1,589 @@
+// gn_iterate.cu -- a2..a7 of the path: the persistent fused WRGN kernel and gn_run.
+//
+// One cooperative launch runs every iteration of a gn_run call.  Each CTA owns a
+// contiguous range of (internal) rows, balanced by entries + rows, and keeps its rows'
+// v, y, x and (when it fits) its slice of col_idx in shared memory for the whole run.
+// Per iteration k (App. B, weighted state y = v (.) x, B = I + gamma_k A):
+//   gather   s_i = sum_{j in N(i)} y_j      (G lanes per light row, a warp per heavy row)
+//   update   d_i = y_i + gamma_k s_i = (B y)_i;  x_i' = y_i / d_i,  y_i' = v_i x_i'
+//            (d_i <= 1e-9: x_i' = 1/2, the safe division of the appendix module)
+//   check    every c iterations: max |x'-x| and the non-binary count (the stop test) plus
+//            FP64 sums of |x'-x|, w x' (Thm. 4) and y (d/2 - v) (= E~(y), Sec. 3)
+//   barrier  a bounded grid barrier; at a check every CTA then reduces the same per-CTA
+//            partials in the same order, so all CTAs take the same stop decision.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gn_internal.cuh"
+
+namespace gn {
+
+struct IterParams {
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const float* v;       // v_hi
+  const float* vlo;     // v_lo
+  const float* w;
+  const int32_t* part;
+  float* y0;            // holds y^{k_start}
+  float* y1;
+  float* x;             // holds x^{k_start}; receives the final x (internal order)
+  float* ylo;           // low parts of the own weighted states (in and out)
+  CheckPartial* partials;
+  unsigned* bar;
+  int* status;
+  DevInfo* info;
+  int n, nblocks;
+  int k_start, k_end;
+  int gamma_mode;
+  double gamma0, gamma1;
+  int ramp;
+  int check_every;
+  double theta;
+  double tol;
+  int heavy;
+  int rows_pad;
+  long long spin_limit;
+  int unreachable;
+};
+
+static constexpr int kThreads = 1024;
+static constexpr float kSafeDiv = 1e-9f;
+
+template <int G, bool SMEM_CSR>
+__global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int R = P.rows_pad;
+  float* s_sum = reinterpret_cast<float*>(smem);
+  float* s_yh = s_sum + R;   // own weighted state, float pair
+  float* s_yl = s_yh + R;
+  float* s_x = s_yl + R;     // own x (FP32: residual and output)
+  float* s_vh = s_x + R;     // v, float pair
+  float* s_vl = s_vh + R;
+  int* s_rp = reinterpret_cast<int*>(s_vl + R);
+  int* s_heavy = s_rp + R + 4;
+  int* s_ci = s_heavy + R;
+
+  __shared__ int s_nheavy;
+  __shared__ float s_rf[32];
+  __shared__ unsigned s_ru[32];
+  __shared__ double s_rd[3][32];
+  __shared__ unsigned long long s_rh[32];
+  __shared__ int s_decide;
+  __shared__ float s_last_r;
+  __shared__ unsigned s_last_n;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int b = blockIdx.x;
+  const int rb = P.part[b], nr = P.part[b + 1] - rb;
+  const int e0 = P.row_ptr[rb];
+
+  // a failed start-state validation (written before the launch) ends the run at once
+  if (dev::ld_relaxed_int(P.status) != 0) return;
+
+  if (tid == 0) s_nheavy = 0;
+  for (int i = tid; i <= nr; i += blockDim.x) s_rp[i] = P.row_ptr[rb + i] - e0;
+  for (int i = tid; i < nr; i += blockDim.x) {
+    s_vh[i] = P.v[rb + i];
+    s_vl[i] = P.vlo[rb + i];
+    s_yh[i] = P.y0[rb + i];
+    s_yl[i] = P.ylo[rb + i];
+    s_x[i] = P.x[rb + i];
+  }
+  __syncthreads();
+  if (SMEM_CSR) {
+    const int ne = s_rp[nr];
+    for (int e = tid; e < ne; e += blockDim.x) s_ci[e] = P.col_idx[e0 + e];
+  }
+  for (int i = tid; i < nr; i += blockDim.x)
+    if (s_rp[i + 1] - s_rp[i] > P.heavy) s_heavy[atomicAdd(&s_nheavy, 1)] = i;
+  __syncthreads();
+  const int* __restrict__ ci = SMEM_CSR ? s_ci : (P.col_idx + e0);
+  const int nheavy = s_nheavy;
+
+  unsigned long long hits = 0;
+  int parity = 0, slot = 0, stop = 0;
+  unsigned nbar = 0;
+  int k = P.k_start;
+  const int grp = tid / G, gl = tid & (G - 1), ngrp = blockDim.x / G;
+
+  for (; k < P.k_end; ++k) {
+    const double gam_d = dev::gamma_at(P.gamma_mode, P.gamma0, P.gamma1, P.ramp, k);
+    const dev::f2 gam = dev::split_f64(gam_d);
+    const float* __restrict__ yin = parity ? P.y1 : P.y0;
+    float* __restrict__ yout = parity ? P.y0 : P.y1;
+
+    // ---- gather: light rows, G lanes per row
+    for (int base = 0; base < nr; base += ngrp) {
+      const int r = base + grp;
+      float acc = 0.0f;
+      bool mine = false;
+      if (r < nr) {
+        const int a = s_rp[r], c = s_rp[r + 1];
+        if (c - a <= P.heavy) {
+          mine = true;
+          for (int e = a + gl; e < c; e += G) acc += yin[ci[e]];
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (mine && gl == 0) s_sum[r] = acc;
+    }
+    // ---- gather: heavy rows, a warp per row
+    for (int h = warp; h < nheavy; h += nwarps) {
+      const int r = s_heavy[h];
+      const int a = s_rp[r], c = s_rp[r + 1];
+      float acc = 0.0f;
+      for (int e = a + lane; e < c; e += 32) acc += yin[ci[e]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) s_sum[r] = acc;
+    }
+    __syncthreads();
+
+    // ---- update + check partials
+    const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
+    float rmax = 0.0f;
+    unsigned nonbin = 0;
+    double l1 = 0.0, obj = 0.0, en = 0.0;
+    for (int i = tid; i < nr; i += blockDim.x) {
+      // the vertex's own state is a float pair; the neighbour sum is FP32 (what was gathered)
+      const dev::f2 y = {s_yh[i], s_yl[i]};
+      const dev::f2 v = {s_vh[i], s_vl[i]};
+      const float xo = s_x[i];
+      const float sn = s_sum[i];
+      // d = y + gamma s = (B y)_i
+      dev::f2 p = dev::two_prod(gam.hi, sn);
+      p.lo = __fmaf_rn(gam.lo, sn, p.lo);
+      dev::f2 d = dev::two_sum(y.hi, p.hi);
+      d = dev::fast_two_sum(d.hi, __fadd_rn(d.lo, __fadd_rn(y.lo, p.lo)));
+      dev::f2 xn, yn;
+      if (d.hi > kSafeDiv) {
+        xn = dev::div_f2(y, d);          // x' = y / (B y)
+        yn = dev::mul_f2(v, xn);         // y' = v x'
+      } else {
+        xn = {0.5f, 0.0f};               // safe division of the appendix module
+        yn = dev::mul_f2(v, xn);
+        ++hits;
+      }
+      s_yh[i] = yn.hi;
+      s_yl[i] = yn.lo;
+      s_x[i] = xn.hi;
+      yout[rb + i] = yn.hi;
+      if (check) {
+        const float dx = fabsf(xn.hi - xo);
+        rmax = fmaxf(rmax, dx);
+        l1 += (double)dx;
+        obj += (double)P.w[rb + i] * (double)xn.hi;
+        const double yd = (double)y.hi + (double)y.lo;
+        en += yd * (0.5 * ((double)d.hi + (double)d.lo) - ((double)v.hi + (double)v.lo));
+        nonbin += ((double)xn.hi > P.theta && (double)xn.hi < 1.0 - P.theta) ? 1u : 0u;
+      }
+    }
+    if (check) {
+      rmax = dev::warp_max(rmax);
+      nonbin = dev::warp_sum_u(nonbin);
+      l1 = dev::warp_sum_d(l1);
+      obj = dev::warp_sum_d(obj);
+      en = dev::warp_sum_d(en);
+      if (lane == 0) {
+        s_rf[warp] = rmax;
+        s_ru[warp] = nonbin;
+        s_rd[0][warp] = l1;
+        s_rd[1][warp] = obj;
+        s_rd[2][warp] = en;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float r2 = lane < nwarps ? s_rf[lane] : 0.0f;
+        unsigned n2 = lane < nwarps ? s_ru[lane] : 0u;
+        double a2 = lane < nwarps ? s_rd[0][lane] : 0.0;
+        double o2 = lane < nwarps ? s_rd[1][lane] : 0.0;
+        double q2 = lane < nwarps ? s_rd[2][lane] : 0.0;
+        r2 = dev::warp_max(r2);
+        n2 = dev::warp_sum_u(n2);
+        a2 = dev::warp_sum_d(a2);
+        o2 = dev::warp_sum_d(o2);
+        q2 = dev::warp_sum_d(q2);
+        if (lane == 0) {
+          CheckPartial cp;
+          cp.rmax = r2;
+          cp.nonbin = n2;
+          cp.l1 = a2;
+          cp.obj = o2;
+          cp.energy = q2;
+          P.partials[slot * P.nblocks + b] = cp;
+        }
+      }
+    }
+
+    // ---- grid barrier (bounded)
+    ++nbar;
+    const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
+    if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit)) {
+      stop = 2;
+      break;
+    }
+    parity ^= 1;
+
+    // ---- stop test: every CTA reduces the same partials in the same order
+    if (check) {
+      const CheckPartial* cps = P.partials + slot * P.nblocks;
+      float fr = 0.0f;
+      unsigned fn = 0;
+      for (int j = tid; j < P.nblocks; j += blockDim.x) {
+        fr = fmaxf(fr, __ldcg(&cps[j].rmax));
+        fn += __ldcg(&cps[j].nonbin);
+      }
+      fr = dev::warp_max(fr);
+      fn = dev::warp_sum_u(fn);
+      if (lane == 0) {
+        s_rf[warp] = fr;
+        s_ru[warp] = fn;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float tr = 0.0f;
+        unsigned tn = 0;
+        for (int j = 0; j < nwarps; ++j) {
+          tr = fmaxf(tr, s_rf[j]);
+          tn += s_ru[j];
+        }
+        const bool bin_ok = (tn == 0u) && (gam_d * (1.0 - P.theta) > P.theta);
+        const bool res_ok = P.tol >= 0.0 && (double)tr <= P.tol;
+        s_decide = (bin_ok || res_ok) ? 1 : 0;
+        s_last_r = tr;
+        s_last_n = tn;
+      }
+      __syncthreads();
+      stop = s_decide;
+      if (b == 0 && (stop || k + 1 == P.k_end)) {
+        // FP64 summary of the final step, block 0 only, fixed order
+        double a2 = 0.0, o2 = 0.0, q2 = 0.0;
+        if (tid == 0) {
+          for (int j = 0; j < P.nblocks; ++j) {
+            a2 += __ldcg(&cps[j].l1);
+            o2 += __ldcg(&cps[j].obj);
+            q2 += __ldcg(&cps[j].energy);
+          }
+          P.info->resid_inf = s_last_r;
+          P.info->nonbin = s_last_n;
+          P.info->resid_l1 = a2;
+          P.info->objective = o2;
+          P.info->energy = q2;
+          P.info->binary = s_last_n == 0u;
+          P.info->converged = stop;
+        }
+      }
+      slot ^= 1;
+      __syncthreads();
+      if (stop) {
+        ++k;
+        break;
+      }
+    }
+  }
+
+  if (stop == 2) return;  // timeout: the status word says so; leave the state as is
+
+  for (int i = tid; i < nr; i += blockDim.x) {
+    P.x[rb + i] = s_x[i];
+    P.ylo[rb + i] = s_yl[i];
+  }
+  // safe-division count
+  unsigned long long h = dev::warp_sum_ull(hits);
+  if (lane == 0) s_rh[warp] = h;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long t = 0;
+    for (int j = 0; j < nwarps; ++j) t += s_rh[j];
+    if (t) atomicAdd(&P.info->hits, t);
+    if (b == 0) {
+      P.info->iters = k - P.k_start;
+      P.info->final_parity = parity;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// start state: x0 (caller order, or 1/(deg+1)), validation (Def. 1), y0 = v (.) x0
+
+__global__ void k_init_state(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                             const float* __restrict__ v, const float* __restrict__ vlo,
+                             const float* __restrict__ x0, const int32_t* __restrict__ perm,
+                             float* __restrict__ x, float* __restrict__ y, float* __restrict__ ylo,
+                             int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = rp[i], e = rp[i + 1];
+  float xi;
+  if (x0) {
+    xi = x0[perm ? perm[i] : i];
+  } else {
+    xi = __frcp_rn((float)(e - b + 1));
+  }
+  bool bad = !(xi >= 0.0f) || !isfinite(xi);
+  if (x0 && !bad && !(xi > 0.0f)) {
+    // (A + I) x0 > 0: a zero needs a positive neighbour
+    bool pos = false;
+    for (int k = b; k < e && !pos; ++k) pos = x0[perm ? perm[ci[k]] : ci[k]] > 0.0f;
+    bad = !pos;
+  }
+  if (bad) atomicOr(status, DEV_NOT_NORMALIZABLE);
+  x[i] = xi;
+  dev::f2 yy = dev::mul_f2(dev::f2{v[i], vlo[i]}, dev::f2{xi, 0.0f});
+  y[i] = yy.hi;
+  ylo[i] = yy.lo;
+}
+
+__global__ void k_to_caller(int n, const float* __restrict__ x_int, const int32_t* __restrict__ iperm,
+                            float* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float xv = x_int[iperm ? iperm[i] : i];
+  out[i] = fminf(fmaxf(xv, 0.0f), 1.0f);
+}
+
+// ------------------------------------------------------------------------------------------
+
+using KernelFn = void (*)(const IterParams);
+
+static KernelFn pick_kernel(int G, bool smem_csr) {
+#define GN_PICK(g)                                                               \
+  case g:                                                                        \
+    return smem_csr ? (KernelFn)k_gn_persistent<g, true> : (KernelFn)k_gn_persistent<g, false>;
+  switch (G) {
+    GN_PICK(1)
+    GN_PICK(2)
+    GN_PICK(4)
+    GN_PICK(8)
+    GN_PICK(16)
+    GN_PICK(32)
+  }
+#undef GN_PICK
+  return nullptr;
+}
+
+static constexpr size_t kSmemLimit = 220 * 1024;
+
+gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp) {
+  const int n = g->n;
+  const int64_t nnz = g->nnz;
+  const int64_t alpha = 4;  // per-row cost in entry units (row bookkeeping + update)
+  const int64_t total = nnz + alpha * (int64_t)n;
+  int nb = (int)std::min<int64_t>(g->num_sms, std::max<int64_t>(1, (total + 2047) / 2048));
+  // balanced contiguous split of the prefix cost C(i) = rp[i] + alpha i
+  std::vector<int32_t> part(nb + 1);
+  part[0] = 0;
+  for (int b = 1; b < nb; ++b) {
+    const int64_t want = total * b / nb;
+    int lo = part[b - 1], hi = n;  // smallest i with C(i) >= want
+    while (lo < hi) {
+      int mid = lo + (hi - lo) / 2;
+      if ((int64_t)rp[mid] + alpha * mid >= want) hi = mid; else lo = mid + 1;
+    }
+    part[b] = lo;
+  }
+  part[nb] = n;
+  int max_rows = 0;
+  int64_t max_ents = 0;
+  for (int b = 0; b < nb; ++b) {
+    max_rows = std::max(max_rows, part[b + 1] - part[b]);
+    max_ents = std::max<int64_t>(max_ents, (int64_t)rp[part[b + 1]] - rp[part[b]]);
+  }
+  const double avg = n > 0 ? (double)nnz / n : 0.0;
+  int G = 1;
+  while (G < 32 && G * 3 < avg) G <<= 1;
+  g->group = G;
+  g->heavy = 16 * G;
+  g->nblocks = nb;
+  g->max_rows = max_rows;
+  g->max_ents = max_ents;
+  const int R = (max_rows + 3) & ~3;
+  const size_t base = sizeof(float) * 6 * (size_t)R + sizeof(int) * ((size_t)R + 4) + sizeof(int) * (size_t)R;
+  const size_t with_csr = base + sizeof(int) * (size_t)max_ents;
+  g->csr_in_smem = with_csr <= kSmemLimit;
+  g->smem_bytes = g->csr_in_smem ? with_csr : base;
+  if (g->smem_bytes > kSmemLimit)
+    return fail(GN_ERR_TOO_LARGE, "gn_create: a CTA's rows exceed shared memory (graph too large)");
+  g->threads = kThreads;
+  KernelFn fn = pick_kernel(G, g->csr_in_smem);
+  // the attribute is an upper bound shared by every graph that uses this instance
+  GN_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kSmemLimit));
+  int per_sm = 0;
+  GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, g->smem_bytes));
+  if (per_sm < 1 || nb > per_sm * g->num_sms)
+    return fail(GN_ERR_TOO_LARGE, "gn_create: persistent kernel does not fit co-resident");
+  GN_CUDA(cudaMalloc(&g->d_part, sizeof(int32_t) * (nb + 1)));
+  GN_CUDA(cudaMemcpyAsync(g->d_part, part.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice,
+                          g->stream));
+  GN_CUDA(cudaMalloc(&g->d_partials, sizeof(CheckPartial) * 2 * nb));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  return GN_OK;
+}
+
+// gamma_k on the host, same arithmetic as the device (host code is built without FMA
+// contraction)
+double host_gamma(const gn_params& p, int k) {
+  if (p.gamma_mode == GN_GAMMA_FIXED || p.ramp_iters <= 1) return p.gamma1;
+  int kk = k < p.ramp_iters - 1 ? k : p.ramp_iters - 1;
+  double t = (double)kk / (double)(p.ramp_iters - 1);
+  return t * p.gamma1 + (1.0 - t) * p.gamma0;
+}
+
+gn_status init_state(gn_graph* g, const float* x0_dev) {
+  if (g->n == 0) return GN_OK;
+  k_init_state<<<(g->n + 255) / 256, 256, 0, g->stream>>>(g->n, g->d_row_ptr, g->d_col_idx, g->d_v,
+                                                           g->d_vlo, x0_dev, g->d_perm, g->d_x,
+                                                           g->d_y[0], g->d_ylo, &g->d_info->status);
+  g->state_parity = 0;
+  GN_LAUNCHED();
+  GN_CUDA(cudaGetLastError());
+  return GN_OK;
+}
+
+// Runs iterations k_start..k_end-1 from d_y[parity0] / d_x; the caller has zeroed d_info
+// except for a start-state status.  Fills *out from the device summary.
+gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const gn_params& p,
+                         int parity0, DevInfo* out, float* ms, int* kernel_used) {
+  IterParams P;
+  P.row_ptr = g->d_row_ptr;
+  P.col_idx = g->d_col_idx;
+  P.v = g->d_v;
+  P.vlo = g->d_vlo;
+  P.w = g->d_w;
+  P.part = g->d_part;
+  P.y0 = g->d_y[parity0];
+  P.y1 = g->d_y[parity0 ^ 1];
+  P.x = g->d_x;
+  P.ylo = g->d_ylo;
+  P.partials = g->d_partials;
+  P.bar = g->d_bar;
+  P.status = &g->d_info->status;
+  P.info = g->d_info;
+  P.n = g->n;
+  P.nblocks = g->nblocks;
+  P.k_start = k_start;
+  P.k_end = k_end;
+  P.gamma_mode = p.gamma_mode;
+  P.gamma0 = p.gamma0;
+  P.gamma1 = p.gamma1;
+  P.ramp = p.ramp_iters;
+  P.check_every = p.check_every;
+  P.theta = p.theta_bin;
+  P.tol = tol;
+  P.heavy = g->heavy;
+  P.rows_pad = (g->max_rows + 3) & ~3;
+  P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
+  P.unreachable = p.debug_unreachable_barrier ? 1 : 0;
+  KernelFn fn = pick_kernel(g->group, g->csr_in_smem);
+  GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned), g->stream));
+  void* args[] = {(void*)&P};
+  GN_CUDA(cudaEventRecord(g->ev0, g->stream));
+  GN_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(g->nblocks), dim3(g->threads), args,
+                                      g->smem_bytes, g->stream));
+  GN_LAUNCHED();
+  GN_CUDA(cudaEventRecord(g->ev1, g->stream));
+  GN_CUDA(cudaMemcpyAsync(out, g->d_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  if (ms) GN_CUDA(cudaEventElapsedTime(ms, g->ev0, g->ev1));
+  if (kernel_used) *kernel_used = GN_KERNEL_PERSISTENT;
+  return GN_OK;
+}
+
+}  // namespace gn
+
+// ------------------------------------------------------------------------------------------
+
+extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double tol,
+                            const gn_params* pin, int start_iter, float* x_out, gn_run_info* info) {
+  using namespace gn;
+  if (!g) return fail(GN_ERR_ARG, "gn_run: NULL handle");
+  gn_params p;
+  if (pin) p = *pin; else gn_default_params(&p);
+  if (start_iter < 0 || max_iters < start_iter || p.check_every < 1 || !(p.theta_bin < 0.5) ||
+      !std::isfinite(p.gamma0) || !std::isfinite(p.gamma1) || p.gamma1 < 0 || p.gamma0 < 0 ||
+      (p.gamma_mode != GN_GAMMA_PURSUIT && p.gamma_mode != GN_GAMMA_FIXED) ||
+      p.kernel < GN_KERNEL_AUTO || p.kernel > GN_KERNEL_CTA)
+    return fail(GN_ERR_ARG, "gn_run: bad argument");
+  GN_CUDA(cudaSetDevice(g->device));
+  GN_CUDA(cudaMemsetAsync(g->d_info, 0, sizeof(DevInfo), g->stream));
+  gn_status st = GN_OK;
+  if (p.resume) {
+    if (!g->has_state) return fail(GN_ERR_ARG, "gn_run: resume without a previous run on this handle");
+  } else {
+    const float* x0_dev = nullptr;
+    if (x0) {
+      st = upload_or_alias(g, x0, sizeof(float) * g->n, (const void**)&x0_dev);
+      if (st != GN_OK) return st;
+    }
+    st = init_state(g, x0_dev);
+    if (st != GN_OK) return st;
+  }
+  const int parity0 = g->state_parity;
+
+  DevInfo di;
+  memset(&di, 0, sizeof di);
+  float ms = 0.0f;
+  int kused = GN_KERNEL_PERSISTENT;
+  if ((int64_t)(max_iters - start_iter) * g->nblocks >= (int64_t)1 << 31)
+    return fail(GN_ERR_TOO_LARGE, "gn_run: too many iterations for one call; split the run with start_iter");
+  if (max_iters > start_iter && g->n > 0) {
+    st = run_iterations(g, start_iter, max_iters, tol, p, parity0, &di, &ms, &kused);
+    if (st != GN_OK) return st;
+    if (!(di.status & DEV_TIMEOUT)) g->state_parity = parity0 ^ di.final_parity;
+  } else {
+    GN_CUDA(cudaMemcpyAsync(&di, g->d_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+    if (di.status == 0 && g->n > 0) {
+      st = state_stats(g, g->d_x, p.theta_bin, &di.objective, &di.nonbin);
+      if (st != GN_OK) return st;
+      di.binary = di.nonbin == 0;
+    }
+  }
+  if (di.status & DEV_NOT_NORMALIZABLE)
+    return fail(GN_ERR_NOT_NORMALIZABLE, "gn_run: x0 is negative, not finite or not normalizable");
+  if (di.status & DEV_TIMEOUT)
+    return fail(GN_ERR_TIMEOUT, "gn_run: a grid-barrier wait hit its limit; the run was abandoned");
+  g->has_state = true;
+
+  gn_status result;
+  if (di.iters == 0) {
+    di.converged = 0;
+    result = GN_WARN_NOT_CONVERGED;
+  } else if (!di.converged) {
+    result = GN_WARN_NOT_CONVERGED;
+  } else {
+    const double gl = host_gamma(p, start_iter + di.iters - 1);
+    result = (di.nonbin == 0 && gl * (1.0 - p.theta_bin) > p.theta_bin) ? GN_OK : GN_WARN_NOT_BINARY;
+  }
+
+  if (x_out && g->n > 0) {
+    float* tmp = g->io_mem == GN_DEVICE ? x_out : g->d_io;
+    k_to_caller<<<(g->n + 255) / 256, 256, 0, g->stream>>>(g->n, g->d_x, g->d_iperm, tmp);
+    GN_LAUNCHED();
+    GN_CUDA(cudaGetLastError());
+    if (g->io_mem == GN_HOST) {
+      GN_CUDA(cudaMemcpyAsync(x_out, tmp, sizeof(float) * g->n, cudaMemcpyDeviceToHost, g->stream));
+    }
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->iters = di.iters;
+    info->converged = di.converged;
+    info->binary = di.binary;
+    info->status = result;
+    info->resid_inf = di.resid_inf;
+    info->resid_l1 = di.resid_l1;
+    info->objective = di.objective;
+    info->energy = di.energy;
+    info->safe_div_hits = (long long)di.hits;
+    info->device_ms = ms;
+    info->kernel = kused;
+  }
+  return result;
+}

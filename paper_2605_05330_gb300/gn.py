@@ -1,0 +1,224 @@
+"""Thin Python binding of libgn.so (include/gn.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the current stream when tensors are passed; numpy arrays use the host I/O
+mode of the C ABI.  Loading fails loudly when the library has not been built: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgn.so")
+
+OK = 0
+WARN_NOT_CONVERGED = 1
+WARN_NOT_BINARY = 2
+WARN_NOT_MAXIMAL = 3
+STATUS = {0: "OK", 1: "WARN_NOT_CONVERGED", 2: "WARN_NOT_BINARY", 3: "WARN_NOT_MAXIMAL",
+          -1: "ERR_ARG", -2: "ERR_NOT_SIMPLE", -3: "ERR_WEIGHT", -4: "ERR_NOT_NORMALIZABLE",
+          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_NOT_INDEPENDENT", -8: "ERR_NO_RECORD",
+          -9: "ERR_TOO_LARGE"}
+HOST, DEVICE = 0, 1
+GAMMA_PURSUIT, GAMMA_FIXED = 0, 1
+REORDER_NONE, REORDER_RCM, REORDER_DEGREE = 0, 1, 2
+KERNEL_AUTO, KERNEL_PERSISTENT, KERNEL_CTA = 0, 1, 2
+
+
+class GNError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = STATUS.get(status, status)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("gamma_mode", ctypes.c_int), ("gamma0", ctypes.c_double), ("gamma1", ctypes.c_double),
+                ("ramp_iters", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("theta_bin", ctypes.c_double), ("kernel", ctypes.c_int), ("record", ctypes.c_int),
+                ("spin_limit", ctypes.c_longlong), ("debug_unreachable_barrier", ctypes.c_int),
+                ("resume", ctypes.c_int)]
+
+
+class RunInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("binary", ctypes.c_int),
+                ("status", ctypes.c_int), ("resid_inf", ctypes.c_double), ("resid_l1", ctypes.c_double),
+                ("objective", ctypes.c_double), ("energy", ctypes.c_double),
+                ("safe_div_hits", ctypes.c_longlong), ("device_ms", ctypes.c_float),
+                ("kernel", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["status"] = STATUS.get(d["status"], d["status"])
+        return d
+
+
+_lib = None
+P = ctypes.c_void_p
+
+
+def lib():
+    """Loads libgn.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_05330_gb300/build.py "
+                              "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.gn_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.gn_default_params.restype = None
+        L.gn_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, P, P, P, ctypes.c_int, ctypes.c_int, P]
+        L.gn_create.restype = ctypes.c_int
+        L.gn_destroy.argtypes = [P]
+        L.gn_destroy.restype = None
+        L.gn_set_io.argtypes = [P, ctypes.c_int]
+        L.gn_set_io.restype = ctypes.c_int
+        L.gn_num_vertices.argtypes = [P]
+        L.gn_num_vertices.restype = ctypes.c_int32
+        L.gn_num_entries.argtypes = [P]
+        L.gn_num_entries.restype = ctypes.c_int64
+        L.gn_run.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Params), ctypes.c_int, P,
+                             ctypes.POINTER(RunInfo)]
+        L.gn_run.restype = ctypes.c_int
+        L.gn_extract_is.argtypes = [P, P, P, P, P, P]
+        L.gn_extract_is.restype = ctypes.c_int
+        L.gn_objective.argtypes = [P, P, ctypes.c_double, P, P]
+        L.gn_objective.restype = ctypes.c_int
+        L.gn_backward.argtypes = [P, P, P, P]
+        L.gn_backward.restype = ctypes.c_int
+        L.gn_last_error.argtypes = []
+        L.gn_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().gn_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _check(st, allow_warn=True):
+    if st < 0 or (st > 0 and not allow_warn):
+        raise GNError(st, lib().gn_last_error().decode())
+    return STATUS[st]
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_of(t):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+class Graph:
+    """A graph resident on the GPU (gn_create).  Pass numpy arrays (host I/O mode) or CUDA
+    tensors (device I/O mode, current stream)."""
+
+    def __init__(self, row_ptr, col_idx, w, reorder=REORDER_NONE, stream=None):
+        self._h = P()
+        self.device_io = _is_torch(row_ptr) and row_ptr.is_cuda
+        if self.device_io:
+            import torch
+            row_ptr = row_ptr.to(torch.int32).contiguous()
+            col_idx = col_idx.to(torch.int32).contiguous()
+            w = w.to(torch.float32).contiguous()
+            st_ptr = stream if stream is not None else _stream_of(row_ptr)
+            self.device = row_ptr.device
+        else:
+            row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            st_ptr = stream
+            self.device = None
+        self.n = int(row_ptr.shape[0]) - 1
+        ci = col_idx if col_idx.shape[0] > 0 else None
+        st = lib().gn_create(ctypes.byref(self._h), self.n, _ptr(row_ptr), _ptr(ci), _ptr(w),
+                             DEVICE if self.device_io else HOST, int(reorder), st_ptr)
+        _check(st)
+        self.nnz = int(lib().gn_num_entries(self._h))
+
+    def close(self):
+        if self._h:
+            lib().gn_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_io(self, device: bool):
+        _check(lib().gn_set_io(self._h, DEVICE if device else HOST))
+        self.device_io = device
+
+    def _alloc(self, dtype, n):
+        if self.device_io:
+            import torch
+            tdt = {np.float32: torch.float32, np.uint8: torch.uint8, np.int32: torch.int32}[dtype]
+            return torch.empty(max(n, 1), dtype=tdt, device=self.device)
+        return np.empty(max(n, 1), dtype=dtype)
+
+    def run(self, x0=None, max_iters=2000, tol=1e-7, params: Params | None = None, start_iter=0,
+            out=True, raise_on_warn=False):
+        """Iterated WRGN (gn_run).  Returns (x, info dict); x is None when out=False."""
+        p = params if params is not None else default_params()
+        x = self._alloc(np.float32, self.n) if out else None
+        if x0 is not None and not self.device_io:
+            x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        info = RunInfo()
+        st = lib().gn_run(self._h, _ptr(x0), int(max_iters), float(tol), ctypes.byref(p), int(start_iter),
+                          _ptr(x), ctypes.byref(info))
+        _check(st, allow_warn=not raise_on_warn)
+        d = info.as_dict()
+        d["status"] = STATUS[st]
+        return (x[: self.n] if x is not None else None), d
+
+    def extract_is(self, x=None):
+        """Rounded set of x (or of the last run's state): (status, mask, members, count, W)."""
+        mask = self._alloc(np.uint8, self.n)
+        members = self._alloc(np.int32, self.n)
+        cnt = ctypes.c_int32(0)
+        wt = ctypes.c_double(0.0)
+        if x is not None and not self.device_io:
+            x = np.ascontiguousarray(x, dtype=np.float32)
+        st = lib().gn_extract_is(self._h, _ptr(x), _ptr(mask), _ptr(members),
+                                 ctypes.cast(ctypes.pointer(cnt), P), ctypes.cast(ctypes.pointer(wt), P))
+        if st < 0 and st != -7:
+            _check(st)
+        return STATUS[st], mask[: self.n], members[: cnt.value], cnt.value, wt.value
+
+    def objective(self, x=None, gamma=1.5):
+        """FP64 (sum w x, E~(v x)) of x (or of the last run's state)."""
+        o = ctypes.c_double(0.0)
+        e = ctypes.c_double(0.0)
+        if x is not None and not self.device_io:
+            x = np.ascontiguousarray(x, dtype=np.float32)
+        _check(lib().gn_objective(self._h, _ptr(x), float(gamma), ctypes.cast(ctypes.pointer(o), P),
+                                  ctypes.cast(ctypes.pointer(e), P)))
+        return o.value, e.value
+
+    def backward(self, dL_dxT, want_w=True, want_x0=True):
+        """Reverse mode of the last recorded run (gn_backward): (dL/dw, dL/dx0)."""
+        gw = self._alloc(np.float32, self.n) if want_w else None
+        gx = self._alloc(np.float32, self.n) if want_x0 else None
+        if not self.device_io:
+            dL_dxT = np.ascontiguousarray(dL_dxT, dtype=np.float32)
+        _check(lib().gn_backward(self._h, _ptr(dL_dxT), _ptr(gw), _ptr(gx)))
+        return (gw[: self.n] if gw is not None else None), (gx[: self.n] if gx is not None else None)

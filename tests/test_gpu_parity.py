@@ -1,0 +1,249 @@
+"""GPU (CUDA path, through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bar (stated by the target of this build): per-vertex |x_gpu - x_oracle| <= 1e-5 *
+max(|x_oracle|, 1e-6) after k in {1, 5, 20} iterations; identical final independent sets
+on instances without near-ties (the oracle returns the same set from x0 and from two
+relative perturbations x0 (1 +- 1e-3 u)); 100% valid (independent) sets.  Integer
+outputs (masks, member lists, counts) are compared bit-exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_05330_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+FLOOR = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_05330_gb300 import build
+    build.build()
+    from paper_2605_05330_gb300 import gn as gnmod
+    return gnmod
+
+
+def dev_graph(gn, inst, reorder=0):
+    import torch
+    return gn.Graph(torch.from_numpy(inst.row_ptr).cuda(), torch.from_numpy(inst.col_idx).cuda(),
+                    torch.from_numpy(inst.w).cuda(), reorder=reorder)
+
+
+def host_graph(gn, inst, reorder=0):
+    return gn.Graph(inst.row_ptr, inst.col_idx, inst.w, reorder=reorder)
+
+
+def to_np(x):
+    return x.detach().cpu().numpy() if hasattr(x, "detach") else np.asarray(x)
+
+
+def assert_close_rel(xg, xo, rel=REL, floor=FLOOR):
+    xg = np.asarray(xg, dtype=np.float64)
+    err = np.abs(xg - xo)
+    bound = rel * np.maximum(np.abs(xo), floor)
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"{bad.size} vertices off, worst rel {np.max(err / np.maximum(np.abs(xo), floor)):.3e}"
+
+
+def fixed_steps(k, gamma_mode=0):
+    # theta < 0 makes every value count as non-binary and tol < 0 disables the residual test,
+    # so exactly k iterations run
+    return dict(max_iters=k, tol=-1.0), dict(theta_bin=-1.0, gamma_mode=gamma_mode, check_every=1)
+
+
+@pytest.mark.parametrize("k", [1, 5, 20])
+@pytest.mark.parametrize("which", ["er2000", "udg20k", "ba20k", "assign24"])
+def test_iterates_match_oracle(gn, which, k):
+    inst = {"er2000": lambda: inputs.workload_er_small(),
+            "udg20k": lambda: inputs.unit_disk_graph(20000, 100000, 1240),
+            "ba20k": lambda: inputs.ba_graph(20000, 5, 1241),
+            "assign24": lambda: inputs.assignment_graph(24, 1242)}[which]()
+    g = dev_graph(gn, inst)
+    run_kw, pk = fixed_steps(k)
+    x, info = g.run(params=gn.default_params(**pk), **run_kw)
+    assert info["iters"] == k
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, p=oracle.params(**pk), **run_kw)
+    assert_close_rel(to_np(x), xo)
+    assert info["safe_div_hits"] == io["safe_div_hits"] == 0
+    assert abs(info["objective"] - io["objective"]) <= 1e-6 * abs(io["objective"])
+
+
+def _tie_free(inst, p, max_iters=3000):
+    deg = np.diff(inst.row_ptr).astype(np.float64)
+    x0 = 1.0 / (deg + 1.0)
+    sets = []
+    u = np.random.default_rng(7).random(inst.n)
+    for s in (0.0, 1e-3, -1e-3):
+        x, info = oracle.run(inst.row_ptr, inst.col_idx, inst.w, x0=x0 * (1 + s * u), max_iters=max_iters, p=p)
+        sets.append(oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, x)[1])
+    return all(np.array_equal(sets[0], t) for t in sets[1:])
+
+
+@pytest.mark.parametrize("seed", [1234, 1300, 1301, 1302])
+def test_final_set_matches_oracle_er2000(gn, seed):
+    inst = inputs.er_graph(2000, 10.0, seed)
+    p = dict(check_every=10)
+    g = dev_graph(gn, inst)
+    x, info = g.run(max_iters=2000, tol=1e-7, params=gn.default_params(**p))
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=2000, tol=1e-7, p=oracle.params(**p))
+    assert info["status"] == "OK" and io["status"] == "OK"
+    st, mask, members, cnt, W = g.extract_is()
+    assert st in ("OK", "WARN_NOT_MAXIMAL")
+    sto, masko, memo, Wo = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, to_np(x))
+    # the GPU extraction agrees bit for bit with the oracle's on the GPU state
+    assert sto == st
+    np.testing.assert_array_equal(to_np(mask), masko)
+    np.testing.assert_array_equal(to_np(members), memo)
+    assert abs(W - Wo) <= 1e-12 * Wo
+    if _tie_free(inst, oracle.params(**p)):
+        np.testing.assert_array_equal(to_np(mask), oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)[1])
+        assert info["iters"] == io["iters"]
+    assert abs(info["objective"] - io["objective"]) <= 1e-3 * io["objective"]
+
+
+@pytest.mark.parametrize("reorder", [1, 2])
+def test_reorder_is_internal(gn, reorder):
+    inst = inputs.unit_disk_graph(30000, 150000, 1250)
+    run_kw, pk = fixed_steps(5)
+    g0 = dev_graph(gn, inst)
+    g1 = dev_graph(gn, inst, reorder=reorder)
+    x0, _ = g0.run(params=gn.default_params(**pk), **run_kw)
+    x1, _ = g1.run(params=gn.default_params(**pk), **run_kw)
+    xo, _ = oracle.run(inst.row_ptr, inst.col_idx, inst.w, p=oracle.params(**pk), **run_kw)
+    assert_close_rel(to_np(x1), xo)
+    assert_close_rel(to_np(x0), xo)
+    xa, ia = g1.run(max_iters=2000)
+    st, mask, members, cnt, W = g1.extract_is()
+    sto, masko, memo, Wo = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, to_np(xa))
+    np.testing.assert_array_equal(to_np(mask), masko)
+    np.testing.assert_array_equal(to_np(members), memo)
+
+
+def test_host_io_mode_matches_device_mode(gn):
+    inst = inputs.er_graph(5000, 8.0, 1260)
+    gd = dev_graph(gn, inst)
+    gh = host_graph(gn, inst)
+    xd, idd = gd.run(max_iters=2000)
+    xh, ih = gh.run(max_iters=2000)
+    np.testing.assert_array_equal(to_np(xd), xh)
+    assert idd["iters"] == ih["iters"]
+    sh = gh.extract_is()
+    sd = gd.extract_is()
+    np.testing.assert_array_equal(to_np(sd[1]), sh[1])
+    assert sd[3] == sh[3] and sd[4] == sh[4]
+
+
+def test_resume_is_bit_exact(gn):
+    """params.resume continues from the handle's full-precision state: a run split at
+    iteration 170 equals the uninterrupted run bit for bit."""
+    inst = inputs.er_graph(3000, 9.0, 1270)
+    p = gn.default_params(check_every=10)
+    g = dev_graph(gn, inst)
+    xf, inf = g.run(max_iters=400, tol=-1.0, params=p)
+    xa, ia = g.run(max_iters=170, tol=-1.0, params=p)
+    xb, ib = g.run(max_iters=400, tol=-1.0, params=gn.default_params(check_every=10, resume=1),
+                   start_iter=170)
+    np.testing.assert_array_equal(to_np(xb), to_np(xf))
+    assert ia["iters"] + ib["iters"] == inf["iters"]
+
+
+def test_resume_from_saved_fp32_state(gn):
+    """Resuming from a saved FP32 x^K (start_iter = K) ends on the same independent set."""
+    inst = inputs.er_graph(3000, 9.0, 1271)
+    g = dev_graph(gn, inst)
+    xf, inf = g.run(max_iters=2000)
+    xa, ia = g.run(max_iters=300, tol=-1.0)
+    xb, ib = g.run(x0=xa.clone(), max_iters=2000, start_iter=300)
+    assert inf["status"] == ib["status"] == "OK"
+    np.testing.assert_array_equal(to_np(xb) > 0.5, to_np(xf) > 0.5)
+
+
+def test_user_x0_and_validation_errors(gn):
+    import torch
+    inst = inputs.er_graph(500, 6.0, 1280)
+    g = dev_graph(gn, inst)
+    x0 = torch.from_numpy(inputs.uniforms(inst.n, 5)).cuda()
+    x, info = g.run(x0=x0, max_iters=20, tol=-1, params=gn.default_params(theta_bin=-1.0, check_every=1))
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, x0=to_np(x0), max_iters=20, tol=-1,
+                        p=oracle.params(theta_bin=-1.0, check_every=1))
+    assert_close_rel(to_np(x), xo)
+    bad = x0.clone()
+    bad[3] = -1.0
+    with pytest.raises(gn.GNError) as e:
+        g.run(x0=bad)
+    assert e.value.status == "ERR_NOT_NORMALIZABLE"
+    z = torch.zeros(inst.n, device="cuda")
+    with pytest.raises(gn.GNError) as e:
+        g.run(x0=z)
+    assert e.value.status == "ERR_NOT_NORMALIZABLE"
+    # the handle stays usable
+    x, info = g.run()
+    assert info["status"] == "OK"
+
+
+def test_invalid_graphs_rejected(gn):
+    with pytest.raises(gn.GNError) as e:
+        gn.Graph(np.array([0, 1, 1]), np.array([1]), np.ones(2))
+    assert e.value.status == "ERR_NOT_SIMPLE"
+    with pytest.raises(gn.GNError) as e:
+        gn.Graph(np.array([0, 1, 2]), np.array([0, 0]), np.ones(2))
+    assert e.value.status == "ERR_NOT_SIMPLE"
+    with pytest.raises(gn.GNError) as e:
+        gn.Graph(np.array([0, 2, 4]), np.array([1, 1, 0, 0]), np.ones(2))
+    assert e.value.status == "ERR_NOT_SIMPLE"
+    with pytest.raises(gn.GNError) as e:
+        gn.Graph(np.array([0, 1, 2]), np.array([1, 0]), np.array([1.0, 0.0]))
+    assert e.value.status == "ERR_WEIGHT"
+    with pytest.raises(gn.GNError) as e:
+        gn.Graph(np.array([0, 1, 2]), np.array([1, 7]), np.ones(2))
+    assert e.value.status == "ERR_ARG"
+
+
+def test_barrier_timeout_returns_status(gn):
+    """A wait that nothing satisfies hits its limit and returns GN_ERR_TIMEOUT; the context
+    stays usable."""
+    inst = inputs.er_graph(20000, 8.0, 1290)
+    g = dev_graph(gn, inst)
+    p = gn.default_params(debug_unreachable_barrier=1, spin_limit=2000)
+    with pytest.raises(gn.GNError) as e:
+        g.run(params=p)
+    assert e.value.status == "ERR_TIMEOUT"
+    x, info = g.run()
+    assert info["status"] == "OK"
+
+
+@pytest.mark.parametrize("case", ["empty", "edgeless", "k2", "star5000", "isolated_mix", "zero_iters"])
+def test_edge_cases(gn, case):
+    if case == "empty":
+        inst = inputs.small_graph("E0", 0, [])
+    elif case == "edgeless":
+        inst = inputs.small_graph("E7", 7, [], w=np.arange(1, 8))
+    elif case == "k2":
+        inst = inputs.small_graph("K2", 2, [(0, 1)], w=[4.0, 1.0])
+    elif case == "star5000":
+        inst = inputs.small_graph("S", 5001, [(0, i) for i in range(1, 5001)],
+                                  w=np.random.default_rng(3).uniform(1, 100, 5001))
+    else:
+        parts = [inputs.er_graph(700, 4, 1291), inputs.small_graph("iso", 50, []), inputs.ba_graph(900, 3, 1292)]
+        inst = inputs.disjoint_union(parts)
+    g = host_graph(gn, inst)
+    if case == "empty":
+        x, info = g.run()
+        assert x.size == 0
+        return
+    if case == "zero_iters":
+        x, info = g.run(max_iters=0)
+        assert info["iters"] == 0 and info["status"] == "WARN_NOT_CONVERGED"
+        return
+    x, info = g.run(max_iters=3000)
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=3000, p=oracle.params(check_every=10))
+    assert info["status"] == io["status"]
+    st, mask, members, cnt, W = g.extract_is()
+    np.testing.assert_array_equal(mask, oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)[1])
+    assert st == "OK"
