@@ -193,6 +193,35 @@ gn_status gn_objective(gn_graph* g, const float* x, double gamma, double* obj, d
  */
 gn_status gn_backward(gn_graph* g, const float* dL_dxT, float* dL_dw, float* dL_dx0);
 
+/*
+ * gn_run_noalloc -- gn_run for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the same persistent iteration kernel.
+ *
+ * Some callers are handed device buffers by a host runtime and may not call cudaMalloc
+ * themselves (a plugin inside another framework's memory pool, a service that allocates
+ * everything at start-up, work issued while the allocator is locked).  This entry point
+ * allocates nothing: no cudaMalloc, no cudaFree, no handle.  All of the kernel's scratch
+ * (weighted states, v = sqrt(w) as a float pair, per-CTA check partials, the grid-barrier
+ * counter, the run summary) lives in one fixed array of about 1.3 MB in the library's device
+ * globals, which every GPU that loads the library holds until the process exits.
+ *   n, row_ptr, col_idx, w   the graph, DEVICE pointers, same layout and rules as gn_create;
+ *                            n <= 65536 (GN_ERR_TOO_LARGE beyond); the CSR is validated on the
+ *                            device (range, order, self-loops, symmetry, weights)
+ *   x0, max_iters, tol, p, start_iter, info   as gn_run (DEVICE x0 or NULL); p->resume is
+ *                            not available (GN_ERR_ARG)
+ *   x_out                    float32[n] DEVICE output, also used as the working x
+ *   stream                   cudaStream_t for all the work (NULL = default stream)
+ * Results equal gn_run's for the same inputs.  Calls share the fixed array and leave their
+ * contents in it: calls whose device work overlaps (several host threads or streams) race and
+ * must be serialised by the caller.  The first call on each device resolves the array's
+ * address with cudaGetSymbolAddress and sets a kernel attribute; make it before any stream
+ * capture.  Returns the same codes as gn_run, plus GN_ERR_ARG / GN_ERR_NOT_SIMPLE /
+ * GN_ERR_WEIGHT for a bad graph.
+ */
+gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* w,
+                         const float* x0, int max_iters, double tol, const gn_params* p,
+                         int start_iter, float* x_out, gn_run_info* info, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles,
  * all threads).  Lets a caller count the device work behind a sequence of calls. */
 int64_t gn_kernel_launches(void);

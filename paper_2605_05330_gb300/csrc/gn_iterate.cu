@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "gn_internal.cuh"
@@ -584,6 +585,312 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
     info->safe_div_hits = (long long)di.hits;
     info->device_ms = ms;
     info->kernel = kused;
+  }
+  return result;
+}
+
+// ==========================================================================================
+// gn_run_noalloc: the persistent iteration without any device allocation.
+//
+// Who needs this: code that is handed device buffers by a host runtime and may not allocate
+// device memory itself -- for instance a plugin or custom operator living inside another
+// framework's memory pool, a real-time service that allocates everything at start-up, or a
+// caller that issues work while the process's allocator is locked.  gn_create allocates the
+// handle's buffers with cudaMalloc; this entry point instead carves every scratch buffer the
+// persistent kernel needs (weighted states, v as a float pair, per-CTA check partials, the
+// grid-barrier counter, the run summary) out of one fixed array in the library's device
+// globals, which every GPU that loads the library holds until the process exits.
+//
+// Consequences a caller must respect:
+//   - at most kNoAllocMaxN vertices (larger graphs are rejected with GN_ERR_TOO_LARGE);
+//   - every call on a device shares the same array and leaves its contents behind, so calls
+//     whose device work overlaps (two host threads, or two streams) race and corrupt each
+//     other: serialise them;
+//   - the first call on each device resolves the array's device address with
+//     cudaGetSymbolAddress (and sets the kernel's shared-memory attribute), so make that first
+//     call before any stream capture begins.
+namespace gn {
+
+static constexpr int kNoAllocMaxN = 65536;
+static constexpr int kNoAllocMaxCTAs = 256;
+static constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+static constexpr size_t kNaVec = align256(sizeof(float) * kNoAllocMaxN);
+static constexpr size_t kNaOffY0 = 0;
+static constexpr size_t kNaOffY1 = kNaOffY0 + kNaVec;
+static constexpr size_t kNaOffYlo = kNaOffY1 + kNaVec;
+static constexpr size_t kNaOffV = kNaOffYlo + kNaVec;
+static constexpr size_t kNaOffVlo = kNaOffV + kNaVec;
+static constexpr size_t kNaOffPartials = kNaOffVlo + kNaVec;
+static constexpr size_t kNaOffPart = kNaOffPartials + align256(sizeof(CheckPartial) * 2 * kNoAllocMaxCTAs);
+static constexpr size_t kNaOffInfo = kNaOffPart + align256(sizeof(int32_t) * (kNoAllocMaxCTAs + 1));
+static constexpr size_t kNaOffBar = kNaOffInfo + align256(sizeof(DevInfo));
+static constexpr size_t kNoAllocScratchBytes = kNaOffBar + 256;
+
+// the fixed scratch (about 1.3 MB per device)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// range, order and self-loop check of the caller's CSR (flags go to the run summary's status)
+__global__ void k_na_check_rows(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  if (b < 0 || e < b || (i == 0 && b != 0)) {
+    atomicOr(status, DEV_BAD_CSR);
+    return;
+  }
+  int prev = -1;
+  for (int k = b; k < e; ++k) {
+    int j = ci[k];
+    if (j < 0 || j >= n) {
+      atomicOr(status, DEV_BAD_CSR);
+      return;
+    }
+    if (j == i || j <= prev) atomicOr(status, DEV_NOT_SIMPLE);
+    prev = j;
+  }
+}
+
+// symmetry, only after the range check passed (the kernel reads the flag first)
+__global__ void k_na_check_symmetry(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                    int* status) {
+  if (dev::ld_relaxed_int(status) & DEV_BAD_CSR) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    int j = ci[k];
+    int a = rp[j], b = rp[j + 1] - 1;
+    bool found = false;
+    while (a <= b) {
+      int m = (a + b) >> 1;
+      int c = ci[m];
+      if (c == i) { found = true; break; }
+      if (c < i) a = m + 1; else b = m - 1;
+    }
+    if (!found) {
+      atomicOr(status, DEV_NOT_SIMPLE);
+      return;
+    }
+  }
+}
+
+// v = sqrt(w) as a float pair, start state (x0 or 1/(deg+1), Def. 1 check), equal-rows
+// partition; skipped when the CSR is malformed
+__global__ void k_na_init(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const float* __restrict__ w, const float* __restrict__ x0, float* __restrict__ v,
+                          float* __restrict__ vlo, float* __restrict__ x, float* __restrict__ y,
+                          float* __restrict__ ylo, int32_t* __restrict__ part, int nblocks, int rows_per,
+                          int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // the partition is written first and unconditionally: the iteration kernel reads it
+  // (and returns at once when the status word is set)
+  if (i <= nblocks) part[i] = min(i * rows_per, n);
+  if (dev::ld_relaxed_int(status) & DEV_BAD_CSR) return;
+  if (i >= n) return;
+  float wi = w[i];
+  dev::f2 vv = {1.0f, 0.0f};
+  if (!(wi > 0.0f) || !isfinite(wi)) atomicOr(status, DEV_BAD_WEIGHT);
+  else vv = dev::split_f64(sqrt((double)wi));
+  v[i] = vv.hi;
+  vlo[i] = vv.lo;
+  const int b = rp[i], e = rp[i + 1];
+  float xi = x0 ? x0[i] : __frcp_rn((float)(e - b + 1));
+  bool bad = !(xi >= 0.0f) || !isfinite(xi);
+  if (x0 && !bad && !(xi > 0.0f)) {
+    bool pos = false;
+    for (int k = b; k < e && !pos; ++k) pos = x0[ci[k]] > 0.0f;
+    bad = !pos;
+  }
+  if (bad) atomicOr(status, DEV_NOT_NORMALIZABLE);
+  x[i] = xi;
+  dev::f2 yy = dev::mul_f2(vv, dev::f2{xi, 0.0f});
+  y[i] = yy.hi;
+  ylo[i] = yy.lo;
+}
+
+__global__ void k_na_clamp(int n, float* __restrict__ x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = fminf(fmaxf(x[i], 0.0f), 1.0f);
+}
+
+static std::mutex g_na_mutex;
+static unsigned char* g_na_ptr[64] = {nullptr};
+static int g_na_sms[64] = {0};
+
+}  // namespace gn
+
+extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                    const float* w, const float* x0, int max_iters, double tol,
+                                    const gn_params* pin, int start_iter, float* x_out,
+                                    gn_run_info* info, void* stream_v) {
+  using namespace gn;
+  if (n < 0 || (n > 0 && (!row_ptr || !w || !x_out)))
+    return fail(GN_ERR_ARG, "gn_run_noalloc: bad argument");
+  if (n > kNoAllocMaxN)
+    return fail(GN_ERR_TOO_LARGE, "gn_run_noalloc: n exceeds the fixed scratch (65536 vertices); "
+                                  "use gn_create / gn_run");
+  gn_params p;
+  if (pin) p = *pin; else gn_default_params(&p);
+  if (start_iter < 0 || max_iters < start_iter || p.check_every < 1 || !(p.theta_bin < 0.5) || p.resume ||
+      !std::isfinite(p.gamma0) || !std::isfinite(p.gamma1) || p.gamma1 < 0 || p.gamma0 < 0 ||
+      (p.gamma_mode != GN_GAMMA_PURSUIT && p.gamma_mode != GN_GAMMA_FIXED))
+    return fail(GN_ERR_ARG, "gn_run_noalloc: bad argument (resume is not available without a handle)");
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  int dev_id = 0;
+  GN_CUDA(cudaGetDevice(&dev_id));
+  if (dev_id < 0 || dev_id >= 64) return fail(GN_ERR_ARG, "gn_run_noalloc: device index out of range");
+
+  // one-time set-up per device: the scratch's device address and the kernel attribute
+  unsigned char* base = nullptr;
+  int sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev_id]) {
+      void* ptr = nullptr;
+      GN_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+      GN_CUDA(cudaDeviceGetAttribute(&g_na_sms[dev_id], cudaDevAttrMultiProcessorCount, dev_id));
+      for (int G = 1; G <= 32; G <<= 1)
+        GN_CUDA(cudaFuncSetAttribute((const void*)pick_kernel(G, false),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+      g_na_ptr[dev_id] = static_cast<unsigned char*>(ptr);
+    }
+    base = g_na_ptr[dev_id];
+    sms = g_na_sms[dev_id];
+  }
+  float* s_y0 = reinterpret_cast<float*>(base + kNaOffY0);
+  float* s_y1 = reinterpret_cast<float*>(base + kNaOffY1);
+  float* s_ylo = reinterpret_cast<float*>(base + kNaOffYlo);
+  float* s_v = reinterpret_cast<float*>(base + kNaOffV);
+  float* s_vlo = reinterpret_cast<float*>(base + kNaOffVlo);
+  CheckPartial* s_partials = reinterpret_cast<CheckPartial*>(base + kNaOffPartials);
+  int32_t* s_part = reinterpret_cast<int32_t*>(base + kNaOffPart);
+  DevInfo* s_info = reinterpret_cast<DevInfo*>(base + kNaOffInfo);
+  unsigned* s_bar = reinterpret_cast<unsigned*>(base + kNaOffBar);
+
+  if (n == 0) {
+    if (info) {
+      memset(info, 0, sizeof *info);
+      info->status = GN_WARN_NOT_CONVERGED;
+    }
+    return GN_WARN_NOT_CONVERGED;
+  }
+  int32_t nnz = 0;
+  GN_CUDA(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+  GN_CUDA(cudaStreamSynchronize(stream));
+  if (nnz < 0 || (nnz > 0 && !col_idx)) return fail(GN_ERR_ARG, "gn_run_noalloc: bad row_ptr or col_idx");
+
+  // launch shape: equal row ranges, CSR read from global memory
+  const int nb = std::max(1, std::min({sms, kNoAllocMaxCTAs, (n + 63) / 64}));
+  const int rows_per = (n + nb - 1) / nb;
+  const double avg = (double)nnz / n;
+  int G = 1;
+  while (G < 32 && G * 3 < avg) G <<= 1;
+  const int R = (rows_per + 3) & ~3;
+  const size_t smem = sizeof(float) * 6 * (size_t)R + sizeof(int) * ((size_t)R + 4) + sizeof(int) * (size_t)R;
+  KernelFn fn = pick_kernel(G, false);
+  int per_sm = 0;
+  GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
+  if (per_sm < 1 || nb > per_sm * sms) return fail(GN_ERR_TOO_LARGE, "gn_run_noalloc: kernel does not fit");
+  if ((int64_t)(max_iters - start_iter) * nb >= (int64_t)1 << 31)
+    return fail(GN_ERR_TOO_LARGE, "gn_run_noalloc: too many iterations for one call");
+
+  // what must start at zero: the run summary (status, counters) and the barrier counter
+  GN_CUDA(cudaMemsetAsync(s_info, 0, sizeof(DevInfo), stream));
+  GN_CUDA(cudaMemsetAsync(s_bar, 0, sizeof(unsigned), stream));
+  const unsigned grid = (unsigned)std::max(n, nb + 1);
+  k_na_check_rows<<<(n + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, &s_info->status);
+  GN_LAUNCHED();
+  k_na_check_symmetry<<<(n + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, &s_info->status);
+  GN_LAUNCHED();
+  k_na_init<<<(grid + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, w, x0, s_v, s_vlo, x_out, s_y0,
+                                                     s_ylo, s_part, nb, rows_per, &s_info->status);
+  GN_LAUNCHED();
+  GN_CUDA(cudaGetLastError());
+
+  DevInfo di;
+  memset(&di, 0, sizeof di);
+  float ms = 0.0f;
+  if (max_iters > start_iter) {
+    IterParams P;
+    P.row_ptr = row_ptr;
+    P.col_idx = col_idx;
+    P.v = s_v;
+    P.vlo = s_vlo;
+    P.w = w;
+    P.part = s_part;
+    P.y0 = s_y0;
+    P.y1 = s_y1;
+    P.x = x_out;
+    P.ylo = s_ylo;
+    P.partials = s_partials;
+    P.bar = s_bar;
+    P.status = &s_info->status;
+    P.info = s_info;
+    P.n = n;
+    P.nblocks = nb;
+    P.k_start = start_iter;
+    P.k_end = max_iters;
+    P.gamma_mode = p.gamma_mode;
+    P.gamma0 = p.gamma0;
+    P.gamma1 = p.gamma1;
+    P.ramp = p.ramp_iters;
+    P.check_every = p.check_every;
+    P.theta = p.theta_bin;
+    P.tol = tol;
+    P.heavy = 16 * G;
+    P.rows_pad = R;
+    P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
+    P.unreachable = p.debug_unreachable_barrier ? 1 : 0;
+    void* args[] = {(void*)&P};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool timed = info != nullptr;
+    if (timed) {
+      GN_CUDA(cudaEventCreate(&e0));
+      GN_CUDA(cudaEventCreate(&e1));
+      GN_CUDA(cudaEventRecord(e0, stream));
+    }
+    GN_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(nb), dim3(kThreads), args, smem, stream));
+    GN_LAUNCHED();
+    if (timed) GN_CUDA(cudaEventRecord(e1, stream));
+    k_na_clamp<<<(n + 255) / 256, 256, 0, stream>>>(n, x_out);
+    GN_LAUNCHED();
+    GN_CUDA(cudaMemcpyAsync(&di, s_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, stream));
+    GN_CUDA(cudaStreamSynchronize(stream));
+    if (timed) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
+  } else {
+    GN_CUDA(cudaMemcpyAsync(&di, s_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, stream));
+    GN_CUDA(cudaStreamSynchronize(stream));
+  }
+  if (di.status & DEV_BAD_CSR) return fail(GN_ERR_ARG, "gn_run_noalloc: malformed CSR");
+  if (di.status & DEV_NOT_SIMPLE) return fail(GN_ERR_NOT_SIMPLE, "gn_run_noalloc: graph is not simple");
+  if (di.status & DEV_BAD_WEIGHT) return fail(GN_ERR_WEIGHT, "gn_run_noalloc: weight <= 0 or not finite");
+  if (di.status & DEV_NOT_NORMALIZABLE)
+    return fail(GN_ERR_NOT_NORMALIZABLE, "gn_run_noalloc: x0 is negative, not finite or not normalizable");
+  if (di.status & DEV_TIMEOUT) return fail(GN_ERR_TIMEOUT, "gn_run_noalloc: a grid-barrier wait hit its limit");
+  gn_status result;
+  if (di.iters == 0 || !di.converged) {
+    result = GN_WARN_NOT_CONVERGED;
+  } else {
+    const double gl = host_gamma(p, start_iter + di.iters - 1);
+    result = (di.nonbin == 0 && gl * (1.0 - p.theta_bin) > p.theta_bin) ? GN_OK : GN_WARN_NOT_BINARY;
+  }
+  if (info) {
+    memset(info, 0, sizeof *info);
+    info->iters = di.iters;
+    info->converged = di.converged;
+    info->binary = di.binary;
+    info->status = result;
+    info->resid_inf = di.resid_inf;
+    info->resid_l1 = di.resid_l1;
+    info->objective = di.objective;
+    info->energy = di.energy;
+    info->safe_div_hits = (long long)di.hits;
+    info->device_ms = ms;
+    info->kernel = GN_KERNEL_PERSISTENT;
   }
   return result;
 }
