@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import glob
 import hashlib
 import json
 import os
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="gn", choices=["gn", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", choices=["udg", "ba"], default=None,
+                    help="run one graph of the workload (profiling aid; not a bench line)")
     return ap.parse_args()
 
 
@@ -59,6 +62,11 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+# internal vertex order per graph: RCM for the unit-disk graph (spatial locality that its
+# random labels hide); the BA graph has no such locality and keeps its order
+REORDER = {"udg": 1, "ba": 0}
 
 
 def make_workload(rank: int):
@@ -135,18 +143,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2605_05330_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()
+
+
 def recorded_traffic():
-    """Per-launch DRAM bytes of the persistent kernel from the committed ncu summary, when it
-    was taken on the current kernel source (else null)."""
-    p = os.path.join(ROOT, "profiles", "gn_persistent_traffic.json")
-    src = os.path.join(ROOT, "paper_2605_05330_gb300", "csrc", "gn_iterate.cu")
+    """Per-launch DRAM bytes of the iteration kernel from the committed ncu summary, when it was
+    taken on the current kernel sources (else null)."""
+    p = os.path.join(ROOT, "profiles", "k_gn_halo_udg200k_ba200k.md")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("source_sha256") != h:
+    fields = {}
+    for line in open(p):
+        line = line.strip()
+        for key in ("traffic_bytes_per_launch:", "source_sha256:"):
+            if line.startswith(key):
+                fields[key[:-1]] = line.split(":", 1)[1].strip()
+    if fields.get("source_sha256") != kernel_source_hash():
         return None
-    return d.get("traffic_bytes_per_launch")
+    return float(fields["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in fields else None
 
 
 def cpu_sample(insts, iters_each=150):
@@ -212,11 +230,13 @@ def main():
             dist.barrier()
 
     insts = make_workload(rank)
+    if args.only:
+        insts = [i for i in insts if i.meta["kind"] == args.only]
     dev = torch.device("cuda", local)
     graphs = []
     for inst in insts:
         g = gn.Graph(torch.from_numpy(inst.row_ptr).to(dev), torch.from_numpy(inst.col_idx).to(dev),
-                     torch.from_numpy(inst.w).to(dev))
+                     torch.from_numpy(inst.w).to(dev), reorder=REORDER[inst.meta["kind"]])
         graphs.append(g)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -304,7 +324,7 @@ def main():
             for inst, rp, ci, w, xo, mk, mb in hosts:
                 h = P()
                 st = L.gn_create(ctypes.byref(h), inst.n, P(rp.data_ptr()), P(ci.data_ptr()), P(w.data_ptr()),
-                                 gn.HOST, 0, P(stream.cuda_stream))
+                                 gn.HOST, REORDER[inst.meta["kind"]], P(stream.cuda_stream))
                 assert st == 0, L.gn_last_error()
                 info = gn.RunInfo()
                 p = gn.default_params()
@@ -357,12 +377,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "udg_n200000_e1M+ba_n200000_m5", "parallelism": "replicas" if world > 1 else "single",
+                       "reorder": {"udg": "rcm", "ba": "none"},
                        "graphs": per_graph, "max_iters": MAX_ITERS, "tol": TOL, "check_every": CHECK_EVERY,
                        "gamma": "pursuit 0.9->1.5 over 1000", "l2": "flushed between timed steps (256 MB write)",
                        "reductions": "fp64"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(),
-                         "kernel": "k_gn_persistent", "peak_kind": peak_kind,
+                         "kernel": "k_gn_halo", "peak_kind": peak_kind,
                          "bytes_per_iter": "4 nnz + 4 (n+1) + 12 n"},
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -123,6 +123,23 @@ void gn_default_params(gn_params* p);
 gn_status gn_create(gn_graph** g, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                     const float* w, int mem, int reorder, void* stream);
 
+#define GN_GATHER_AUTO 0      /* the fastest mode that fits (halo, else CSR in smem, else global) */
+#define GN_GATHER_GLOBAL 1    /* neighbour ids and values read through L1/L2 */
+#define GN_GATHER_SMEM_CSR 2  /* each CTA's neighbour ids in shared memory, values through L1/L2 */
+#define GN_GATHER_HALO 3      /* each CTA's distinct external neighbours staged in shared memory */
+
+typedef struct {
+  int reorder;          /* GN_REORDER_* */
+  int gather;           /* GN_GATHER_*; a forced mode that does not fit gives GN_ERR_TOO_LARGE */
+} gn_create_opts;
+
+/* gn_create with options (NULL = reorder none, gather auto).  Same contract as gn_create. */
+gn_status gn_create_ex(gn_graph** g, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                       const float* w, int mem, const gn_create_opts* opts, void* stream);
+
+/* Gather mode the handle's persistent kernel uses (GN_GATHER_GLOBAL, _SMEM_CSR or _HALO). */
+int gn_gather_mode(const gn_graph* g);
+
 /* Releases every resource of the handle (NULL is a no-op). */
 void gn_destroy(gn_graph* g);
 
@@ -202,8 +219,9 @@ gn_status gn_backward(gn_graph* g, const float* dL_dxT, float* dL_dw, float* dL_
  * everything at start-up, work issued while the allocator is locked).  This entry point
  * allocates nothing: no cudaMalloc, no cudaFree, no handle.  All of the kernel's scratch
  * (weighted states, v = sqrt(w) as a float pair, per-CTA check partials, the grid-barrier
- * counter, the run summary) lives in one fixed array of about 1.3 MB in the library's device
- * globals, which every GPU that loads the library holds until the process exits.
+ * counter, the run summary, the gamma schedule) lives in one fixed array of about 1.5 MB in
+ * the library's device globals, which every GPU that loads the library holds until the
+ * process exits.  The gamma pursuit may span at most 16384 table entries.
  *   n, row_ptr, col_idx, w   the graph, DEVICE pointers, same layout and rules as gn_create;
  *                            n <= 65536 (GN_ERR_TOO_LARGE beyond); the CSR is validated on the
  *                            device (range, order, self-loops, symmetry, weights)

@@ -93,25 +93,11 @@ __global__ void k_weights(int n, const float* __restrict__ w, float* __restrict_
   vlo[i] = p.lo;
 }
 
-// permuted CSR: new row r is old row perm[r], neighbours renamed by iperm and re-sorted
-__global__ void k_permute_rows(int n, const int32_t* __restrict__ perm, const int32_t* __restrict__ iperm,
-                               const int32_t* __restrict__ rp_old, const int32_t* __restrict__ ci_old,
-                               const int32_t* __restrict__ rp_new, int32_t* __restrict__ ci_new,
-                               const float* __restrict__ w_old, float* __restrict__ w_new) {
+// permuted weights: new vertex r is old vertex perm[r]
+__global__ void k_permute_w(int n, const int32_t* __restrict__ perm, const float* __restrict__ w_old,
+                            float* __restrict__ w_new) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  int o = perm[r];
-  int b = rp_old[o], e = rp_old[o + 1];
-  int d = rp_new[r];
-  for (int k = b; k < e; ++k) ci_new[d + (k - b)] = iperm[ci_old[k]];
-  // insertion sort of the renamed row (rows are short; hubs pay once at create)
-  for (int a = d + 1; a < d + (e - b); ++a) {
-    int key = ci_new[a];
-    int c = a - 1;
-    while (c >= d && ci_new[c] > key) { ci_new[c + 1] = ci_new[c]; --c; }
-    ci_new[c + 1] = key;
-  }
-  w_new[r] = w_old[o];
+  if (r < n) w_new[r] = w_old[perm[r]];
 }
 
 static unsigned grid_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -213,7 +199,7 @@ extern "C" void gn_destroy(gn_graph* g) {
   void* dptrs[] = {g->d_row_ptr, g->d_col_idx, g->d_w, g->d_v, g->d_vlo, g->d_ylo, g->d_perm, g->d_iperm, g->d_part,
                    g->d_y[0], g->d_y[1], g->d_x, g->d_tmp, g->d_bsum, g->d_io, g->d_partials, g->d_bar, g->d_info,
                    g->d_flags, g->d_red, g->d_mask, g->d_mask_c, g->d_bcount, g->d_bws,
-                   g->d_members};
+                   g->d_members, g->d_hoff, g->d_hblob, g->d_gtab};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (g->h_info) cudaFreeHost(g->h_info);
@@ -226,14 +212,28 @@ extern "C" void gn_destroy(gn_graph* g) {
 }
 
 namespace gn {
-gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp);  // gn_iterate.cu
+gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci);  // gn_iterate.cu
 }
 
 extern "C" gn_status gn_create(gn_graph** out, int32_t n, const int32_t* row_ptr,
                                const int32_t* col_idx, const float* w, int mem, int reorder,
                                void* stream) {
+  gn_create_opts o;
+  o.reorder = reorder;
+  o.gather = GN_GATHER_AUTO;
+  return gn_create_ex(out, n, row_ptr, col_idx, w, mem, &o, stream);
+}
+
+extern "C" int gn_gather_mode(const gn_graph* g) { return g ? g->gather : 0; }
+
+extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_ptr,
+                                  const int32_t* col_idx, const float* w, int mem,
+                                  const gn_create_opts* opts, void* stream) {
   using namespace gn;
+  const int reorder = opts ? opts->reorder : GN_REORDER_NONE;
+  const int gather = opts ? opts->gather : GN_GATHER_AUTO;
   if (!out) return fail(GN_ERR_ARG, "gn_create: out is NULL");
+  if (gather < GN_GATHER_AUTO || gather > GN_GATHER_HALO) return fail(GN_ERR_ARG, "gn_create: bad gather mode");
   *out = nullptr;
   if (n < 0 || !row_ptr || (!w && n > 0) || (mem != GN_HOST && mem != GN_DEVICE) ||
       reorder < GN_REORDER_NONE || reorder > GN_REORDER_DEGREE)
@@ -326,54 +326,68 @@ extern "C" gn_status gn_create(gn_graph** out, int32_t n, const int32_t* row_ptr
                                    "row entries, or asymmetric adjacency)");
   if (g->h_flags[0] & DEV_BAD_WEIGHT) return fail(GN_ERR_WEIGHT, "gn_create: weight <= 0 or not finite");
 
-  // optional locality reordering (internal; undone on every output)
-  if (reorder != GN_REORDER_NONE && n > 1) {
-    std::vector<int32_t> ci(g->nnz);
+  // the CSR on the host: the reordering and the per-CTA halo lists are built from it
+  std::vector<int32_t> ci_host;
+  const int32_t* ci_h = col_idx;
+  if (mem == GN_DEVICE || g->nnz == 0) {
+    ci_host.resize((size_t)std::max<int64_t>(g->nnz, 1));
     if (g->nnz > 0)
-      GN_CUDA(cudaMemcpyAsync(ci.data(), g->d_col_idx, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToHost,
+      GN_CUDA(cudaMemcpyAsync(ci_host.data(), g->d_col_idx, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToHost,
                               g->stream));
     GN_CUDA(cudaStreamSynchronize(g->stream));
+    ci_h = ci_host.data();
+  }
+
+  // optional locality reordering (internal; undone on every output)
+  if (reorder != GN_REORDER_NONE && n > 1) {
     std::vector<int32_t> perm;
+    std::vector<int32_t> ci_src(ci_h, ci_h + g->nnz);
     if (reorder == GN_REORDER_RCM) {
-      rcm_order(n, rp, ci, perm);
+      rcm_order(n, rp, ci_src, perm);
     } else {
       perm.resize(n);
       std::iota(perm.begin(), perm.end(), 0);
       std::stable_sort(perm.begin(), perm.end(),
                        [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
     }
-    std::vector<int32_t> iperm(n), rp2(n + 1);
+    std::vector<int32_t> iperm(n), rp2(n + 1), ci2((size_t)std::max<int64_t>(g->nnz, 1));
     for (int r = 0; r < n; ++r) iperm[perm[r]] = r;
     rp2[0] = 0;
-    for (int r = 0; r < n; ++r) rp2[r + 1] = rp2[r] + (rp[perm[r] + 1] - rp[perm[r]]);
-    int32_t *d_rp2 = nullptr, *d_ci2 = nullptr;
+    for (int r = 0; r < n; ++r) {
+      const int o = perm[r];
+      int32_t* dst = ci2.data() + rp2[r];
+      const int d = rp[o + 1] - rp[o];
+      for (int k = 0; k < d; ++k) dst[k] = iperm[ci_src[rp[o] + k]];
+      std::sort(dst, dst + d);
+      rp2[r + 1] = rp2[r] + d;
+    }
     float* d_w2 = nullptr;
     GN_CUDA(cudaMalloc(&g->d_perm, sizeof(int32_t) * n));
     GN_CUDA(cudaMalloc(&g->d_iperm, sizeof(int32_t) * n));
-    GN_CUDA(cudaMalloc(&d_rp2, sizeof(int32_t) * (n + 1)));
-    GN_CUDA(cudaMalloc(&d_ci2, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1)));
     GN_CUDA(cudaMalloc(&d_w2, sizeof(float) * n));
     GN_CUDA(cudaMemcpyAsync(g->d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
     GN_CUDA(cudaMemcpyAsync(g->d_iperm, iperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
-    GN_CUDA(cudaMemcpyAsync(d_rp2, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, g->stream));
-    k_permute_rows<<<grid_for(n, 128), 128, 0, g->stream>>>(n, g->d_perm, g->d_iperm, g->d_row_ptr,
-                                                            g->d_col_idx, d_rp2, d_ci2, g->d_w, d_w2);
+    GN_CUDA(cudaMemcpyAsync(g->d_row_ptr, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                            g->stream));
+    if (g->nnz > 0)
+      GN_CUDA(cudaMemcpyAsync(g->d_col_idx, ci2.data(), sizeof(int32_t) * g->nnz, cudaMemcpyHostToDevice,
+                              g->stream));
+    k_permute_w<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_perm, g->d_w, d_w2);
     GN_LAUNCHED();
     GN_CUDA(cudaGetLastError());
     GN_CUDA(cudaStreamSynchronize(g->stream));
-    cudaFree(g->d_row_ptr);
-    cudaFree(g->d_col_idx);
     cudaFree(g->d_w);
-    g->d_row_ptr = d_rp2;
-    g->d_col_idx = d_ci2;
     g->d_w = d_w2;
     k_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_w, g->d_v, g->d_vlo, g->d_flags);
     GN_LAUNCHED();
     GN_CUDA(cudaGetLastError());
     rp.swap(rp2);
+    ci_host.swap(ci2);
+    ci_h = ci_host.data();
   }
 
-  gn_status st = configure_partition(g, rp);
+  g->gather = gather;
+  gn_status st = configure_partition(g, rp, ci_h);
   if (st != GN_OK) return st;
   GN_CUDA(cudaStreamSynchronize(g->stream));
   *out = g;

@@ -97,6 +97,14 @@ struct gn_graph {
   int group = 4;                // lanes per light row
   int heavy = 128;              // rows with more entries go warp-per-row
   bool csr_in_smem = false;
+  int mode = 0;                 // gather mode of the persistent kernel (gn_iterate.cu)
+  int gather = 0;               // requested GN_GATHER_* at create, then the one in use
+  int halo_pad = 0;             // padded length of the longest per-CTA halo list
+  int rows_pad_halo = 0;        // padded rows per CTA of the halo layout
+  void* d_gtab = nullptr;       // per-run gamma_k table (float pairs)
+  int gtab_cap = 0;
+  int64_t* d_hoff = nullptr;    // [nblocks + 1] byte offsets of the per-CTA halo blocks
+  unsigned char* d_hblob = nullptr;  // packed per-CTA halo blocks (gn_halo.cu)
   size_t smem_bytes = 0;
   int threads = 1024;
 
@@ -217,43 +225,84 @@ __device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v)
 }
 
 // ---- float-pair ("double-float") arithmetic on the FP32 pipes.  A value is hi + lo with
-// |lo| <= ulp(hi)/2; error-free transforms use round-to-nearest intrinsics so that the
-// compiler cannot contract or reorder them.
+// |lo| <= ulp(hi)/2.  Every operation is explicit round-to-nearest PTX, so the compiler cannot
+// contract or reorder the error-free transforms.  Subnormal values are kept (FP32 add, mul
+// and fma handle them at full rate); the quotient uses an approximate reciprocal plus a
+// correction instead of the IEEE division sequence, whose slow path subnormals would take.
 struct f2 {
   float hi, lo;
 };
+__device__ __forceinline__ float fadd(float a, float b) {
+  float r;
+  asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float fsub(float a, float b) {
+  float r;
+  asm("sub.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float fmul(float a, float b) {
+  float r;
+  asm("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float ffma(float a, float b, float c) {
+  float r;
+  asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float frcp_approx(float a) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 __device__ __forceinline__ f2 two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  float s = fadd(a, b);
+  float bb = fsub(s, a);
+  float e = fadd(fsub(a, fsub(s, bb)), fsub(b, bb));
   return {s, e};
 }
 __device__ __forceinline__ f2 fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
-  float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+  float s = fadd(a, b);
+  return {s, fsub(b, fsub(s, a))};
 }
 __device__ __forceinline__ f2 two_prod(float a, float b) {
-  float p = __fmul_rn(a, b);
-  return {p, __fmaf_rn(a, b, -p)};
+  float p = fmul(a, b);
+  return {p, ffma(a, b, -p)};
 }
 // (a_hi + a_lo) * (b_hi + b_lo), normalised
 __device__ __forceinline__ f2 mul_f2(f2 a, f2 b) {
   f2 p = two_prod(a.hi, b.hi);
-  float c = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
-  return fast_two_sum(p.hi, __fadd_rn(p.lo, c));
+  float c = ffma(a.hi, b.lo, fmul(a.lo, b.hi));
+  return fast_two_sum(p.hi, fadd(p.lo, c));
 }
-// a / b for float pairs (one IEEE division plus one correction step)
+// a / b for float pairs, b.hi a normal number: an approximate reciprocal, a quotient, its exact
+// residual a - q1 b, and one correction (relative error about 2^-44)
 __device__ __forceinline__ f2 div_f2(f2 a, f2 b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
-  f2 t = two_prod(q1, b.hi);
-  float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, t.hi), t.lo), __fsub_rn(a.lo, __fmul_rn(q1, b.lo)));
-  float q2 = __fdiv_rn(r, b.hi);
+  const float r0 = frcp_approx(b.hi);
+  const float q1 = fmul(a.hi, r0);
+  const f2 t = two_prod(q1, b.hi);
+  const float rem = fadd(fsub(fsub(a.hi, t.hi), t.lo), fsub(a.lo, fmul(q1, b.lo)));
+  const float q2 = fmul(rem, r0);
   return fast_two_sum(q1, q2);
 }
 __device__ __forceinline__ f2 split_f64(double v) {
   float hi = __double2float_rn(v);
   return {hi, __double2float_rn(v - (double)hi)};
 }
+// warp sum of float pairs (compensated), for FP64-grade totals on the FP32 pipes
+__device__ __forceinline__ f2 warp_sum_pair(f2 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    f2 s = two_sum(a.hi, oh);
+    a = fast_two_sum(s.hi, fadd(s.lo, fadd(a.lo, ol)));
+  }
+  return a;
+}
+__device__ __forceinline__ f2 warp_sum_f2(float v) { return warp_sum_pair(f2{v, 0.0f}); }
 
 // gamma_k of Sec. 6 / the appendix module, in FP64 (then rounded once to FP32 by callers)
 __device__ __forceinline__ double gamma_at(int mode, double g0, double g1, int T, int k) {

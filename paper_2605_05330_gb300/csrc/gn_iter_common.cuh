@@ -1,0 +1,265 @@
+// gn_iter_common.cuh -- the parts of one WRGN iteration that every gather mode shares:
+// the per-vertex update (App. B weighted state, float-pair own state), the stop-test
+// partials, the bounded grid barrier and the stop decision.
+#pragma once
+
+#include "gn_internal.cuh"
+
+namespace gn {
+
+// launch parameters of the persistent kernels
+struct IterParams {
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const float* v;       // v_hi
+  const float* vlo;     // v_lo
+  const float* w;
+  const int32_t* part;
+  float* y0;            // holds y^{k_start}
+  float* y1;
+  float* x;             // holds x^{k_start}; receives the final x (internal order)
+  float* ylo;           // low parts of the own weighted states (in and out)
+  CheckPartial* partials;
+  unsigned* bar;
+  int* status;
+  DevInfo* info;
+  // halo mode (gn_halo.cu): per-CTA blocks of a packed layout, see HaloLayout
+  const int64_t* hoff;      // [nblocks + 1] byte offsets of each CTA's block in hblob
+  const unsigned char* hblob;
+  const float2* gtab;       // gamma_k as float pairs for k < gtab_len (then the last entry)
+  int gtab_len;
+  int n, nblocks;
+  int k_start, k_end;
+  int gamma_mode;
+  double gamma0, gamma1;
+  int ramp;
+  int check_every;
+  double theta;
+  double tol;
+  int heavy;
+  int rows_pad;
+  int halo_pad;
+  long long spin_limit;
+  int unreachable;
+};
+
+static constexpr int kThreads = 1024;
+static constexpr float kSafeDiv = 1e-9f;
+
+// per-CTA shared arrays of the owned rows
+struct RowArrays {
+  float* sum;   // neighbour sums s_i of this iteration
+  float* yh;    // own weighted state, float pair
+  float* yl;
+  float* x;     // own x (FP32: residual and output)
+  float* vh;    // v = sqrt(w), float pair
+  float* vl;
+};
+
+// per-thread accumulators of the stop test
+struct CheckAcc {
+  float rmax = 0.0f;
+  unsigned nonbin = 0;
+  float l1 = 0.0f, obj = 0.0f, en = 0.0f;
+};
+
+// The update of one row (global id rb + i):
+//   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. WRGN in the weighted state, App. B)
+//   d <= 1e-9: x' = 1/2 (the safe division of the appendix module)
+// and, at a check, its terms of the stop test (FP32 terms, summed as float pairs later).
+__device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x, float sn, dev::f2 gam,
+                                           bool check, float wi, float th_lo, float th_hi,
+                                           unsigned long long& hits, CheckAcc& acc) {
+  dev::f2 p = dev::two_prod(gam.hi, sn);
+  p.lo = dev::ffma(gam.lo, sn, p.lo);
+  dev::f2 d = dev::two_sum(y.hi, p.hi);
+  d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(y.lo, p.lo)));
+  dev::f2 xn;
+  if (d.hi > kSafeDiv) {
+    xn = dev::div_f2(y, d);
+  } else {
+    xn = {0.5f, 0.0f};
+    ++hits;
+  }
+  const dev::f2 yn = dev::mul_f2(v, xn);
+  if (check) {
+    const float dx = fabsf(xn.hi - x);
+    acc.rmax = fmaxf(acc.rmax, dx);
+    acc.l1 += dx;
+    acc.obj = __fmaf_rn(wi, xn.hi, acc.obj);
+    acc.en = __fmaf_rn(y.hi, __fmaf_rn(0.5f, d.hi, -v.hi), acc.en);
+    acc.nonbin += (xn.hi > th_lo && xn.hi < th_hi) ? 1u : 0u;
+  }
+  y = yn;
+  x = xn.hi;
+}
+
+// the update of rows [0, nr) of the CTA with their state in shared memory
+__device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, const float* __restrict__ w,
+                                            float* __restrict__ yout, dev::f2 gam, bool check,
+                                            float th_lo, float th_hi, unsigned long long& hits,
+                                            CheckAcc& acc) {
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    dev::f2 y = {S.yh[i], S.yl[i]};
+    float x = S.x[i];
+    update_one(y, dev::f2{S.vh[i], S.vl[i]}, x, S.sum[i], gam, check, check ? w[rb + i] : 0.0f, th_lo,
+               th_hi, hits, acc);
+    S.yh[i] = y.hi;
+    S.yl[i] = y.lo;
+    S.x[i] = x;
+    yout[rb + i] = y.hi;
+  }
+}
+
+struct TailShared {
+  float gh, gl;     // gamma_k of the coming iteration as a float pair, and in FP64
+  double gd;
+  float rf[32];
+  unsigned ru[32];
+  float rdh[3][32];
+  float rdl[3][32];
+  unsigned long long rh[32];
+  int decide;
+  float last_r;
+  unsigned last_n;
+};
+
+// block reduction of the stop-test accumulators into this CTA's partial of the check slot
+__device__ __forceinline__ void write_check_partial(const IterParams& P, const CheckAcc& a, int slot,
+                                                    TailShared& T) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const float rmax = dev::warp_max(a.rmax);
+  const unsigned nonbin = dev::warp_sum_u(a.nonbin);
+  const dev::f2 l1 = dev::warp_sum_f2(a.l1);
+  const dev::f2 obj = dev::warp_sum_f2(a.obj);
+  const dev::f2 en = dev::warp_sum_f2(a.en);
+  if (lane == 0) {
+    T.rf[warp] = rmax;
+    T.ru[warp] = nonbin;
+    T.rdh[0][warp] = l1.hi;
+    T.rdl[0][warp] = l1.lo;
+    T.rdh[1][warp] = obj.hi;
+    T.rdl[1][warp] = obj.lo;
+    T.rdh[2][warp] = en.hi;
+    T.rdl[2][warp] = en.lo;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const bool in = lane < nwarps;
+    const float r2 = dev::warp_max(in ? T.rf[lane] : 0.0f);
+    const unsigned n2 = dev::warp_sum_u(in ? T.ru[lane] : 0u);
+    dev::f2 q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      q[c] = dev::warp_sum_pair(in ? dev::f2{T.rdh[c][lane], T.rdl[c][lane]} : dev::f2{0.0f, 0.0f});
+    if (lane == 0) {
+      CheckPartial cp;
+      cp.rmax = r2;
+      cp.nonbin = n2;
+      cp.l1 = (double)q[0].hi + (double)q[0].lo;
+      cp.obj = (double)q[1].hi + (double)q[1].lo;
+      cp.energy = (double)q[2].hi + (double)q[2].lo;
+      P.partials[slot * P.nblocks + blockIdx.x] = cp;
+    }
+  }
+}
+
+// Grid barrier, then (at a check) the stop test: every CTA reduces the same partials in the
+// same order, so all take the same decision.  Returns 0 (continue), 1 (stop after this
+// iteration) or 2 (a wait hit its limit).
+__device__ __forceinline__ int barrier_and_stop(const IterParams& P, unsigned& nbar, int& slot, bool check,
+                                                double gam_d, int k, TailShared& T) {
+  ++nbar;
+  const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
+  if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit)) return 2;
+  if (!check) return 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const CheckPartial* cps = P.partials + slot * P.nblocks;
+  float fr = 0.0f;
+  unsigned fn = 0;
+  for (int j = tid; j < P.nblocks; j += blockDim.x) {
+    fr = fmaxf(fr, __ldcg(&cps[j].rmax));
+    fn += __ldcg(&cps[j].nonbin);
+  }
+  fr = dev::warp_max(fr);
+  fn = dev::warp_sum_u(fn);
+  if (lane == 0) {
+    T.rf[warp] = fr;
+    T.ru[warp] = fn;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float tr = 0.0f;
+    unsigned tn = 0;
+    for (int j = 0; j < nwarps; ++j) {
+      tr = fmaxf(tr, T.rf[j]);
+      tn += T.ru[j];
+    }
+    const bool bin_ok = (tn == 0u) && (gam_d * (1.0 - P.theta) > P.theta);
+    const bool res_ok = P.tol >= 0.0 && (double)tr <= P.tol;
+    const int stop = (bin_ok || res_ok) ? 1 : 0;
+    T.decide = stop;
+    if (blockIdx.x == 0 && (stop || k + 1 == P.k_end)) {
+      // FP64 summary of the final step, block 0 only, fixed order
+      double a2 = 0.0, o2 = 0.0, q2 = 0.0;
+      for (int j = 0; j < P.nblocks; ++j) {
+        a2 += __ldcg(&cps[j].l1);
+        o2 += __ldcg(&cps[j].obj);
+        q2 += __ldcg(&cps[j].energy);
+      }
+      P.info->resid_inf = tr;
+      P.info->nonbin = tn;
+      P.info->resid_l1 = a2;
+      P.info->objective = o2;
+      P.info->energy = q2;
+      P.info->binary = tn == 0u;
+      P.info->converged = stop;
+    }
+  }
+  __syncthreads();
+  slot ^= 1;
+  return T.decide;
+}
+
+// gamma_k (Sec. 6) for iteration k from the per-run table (float pair; FP64 value = hi + lo),
+// read by thread 0 and broadcast through shared memory.  The load for iteration k + 1 is
+// issued at the start of iteration k (gamma_fetch) and stored after the update (gamma_store),
+// so its latency hides behind the iteration.
+__device__ __forceinline__ float2 gamma_fetch(const IterParams& P, int k) {
+  return threadIdx.x == 0 ? P.gtab[k < P.gtab_len ? k : P.gtab_len - 1] : make_float2(0.0f, 0.0f);
+}
+__device__ __forceinline__ void gamma_store(float2 g, TailShared& T) {
+  if (threadIdx.x == 0) {
+    T.gh = g.x;
+    T.gl = g.y;
+    T.gd = (double)g.x + (double)g.y;
+  }
+}
+__device__ __forceinline__ void set_gamma(const IterParams& P, int k, TailShared& T) {
+  gamma_store(gamma_fetch(P, k), T);
+}
+
+// end of a run: own x and float-pair low parts back to global memory, safe-division count,
+// iteration count and the parity of the buffer holding the final weighted state
+__device__ __forceinline__ void finish_run(const IterParams& P, const RowArrays& S, int rb, int nr,
+                                           unsigned long long hits, int k, int parity, TailShared& T) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (int i = tid; i < nr; i += blockDim.x) {
+    P.x[rb + i] = S.x[i];
+    P.ylo[rb + i] = S.yl[i];
+  }
+  unsigned long long h = dev::warp_sum_ull(hits);
+  if (lane == 0) T.rh[warp] = h;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long t = 0;
+    for (int j = 0; j < nwarps; ++j) t += T.rh[j];
+    if (t) atomicAdd(&P.info->hits, t);
+    if (blockIdx.x == 0) {
+      P.info->iters = k - P.k_start;
+      P.info->final_parity = parity;
+    }
+  }
+}
+
+}  // namespace gn

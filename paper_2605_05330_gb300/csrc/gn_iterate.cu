@@ -15,66 +15,42 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
-#include "gn_internal.cuh"
+#include "gn_iter_common.cuh"
 
 namespace gn {
 
-struct IterParams {
-  const int32_t* row_ptr;
-  const int32_t* col_idx;
-  const float* v;       // v_hi
-  const float* vlo;     // v_lo
-  const float* w;
-  const int32_t* part;
-  float* y0;            // holds y^{k_start}
-  float* y1;
-  float* x;             // holds x^{k_start}; receives the final x (internal order)
-  float* ylo;           // low parts of the own weighted states (in and out)
-  CheckPartial* partials;
-  unsigned* bar;
-  int* status;
-  DevInfo* info;
-  int n, nblocks;
-  int k_start, k_end;
-  int gamma_mode;
-  double gamma0, gamma1;
-  int ramp;
-  int check_every;
-  double theta;
-  double tol;
-  int heavy;
-  int rows_pad;
-  long long spin_limit;
-  int unreachable;
+// Gather modes of the persistent kernel
+enum GatherMode : int {
+  MODE_GMEM = 0,       // neighbour ids read from global memory, values gathered from L1/L2
+  MODE_SMEM_CSR = 1,   // the CTA's neighbour ids held in shared memory, values from L1/L2
+  MODE_HALO = 2,       // gn_halo.cu: external halo values staged in shared memory
 };
 
-static constexpr int kThreads = 1024;
-static constexpr float kSafeDiv = 1e-9f;
+gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
+                     const std::vector<int32_t>& part, size_t smem_limit, bool* fits);  // gn_halo.cu
+const void* halo_kernel(int rows_pad);
 
+// The generic persistent kernel: values gathered through L1/L2 (MODE_GMEM, MODE_SMEM_CSR),
+// G lanes per light row and a warp per heavy row.
 template <int G, bool SMEM_CSR>
 __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ TailShared T;
+  __shared__ int s_nheavy;
   const int R = P.rows_pad;
-  float* s_sum = reinterpret_cast<float*>(smem);
-  float* s_yh = s_sum + R;   // own weighted state, float pair
-  float* s_yl = s_yh + R;
-  float* s_x = s_yl + R;     // own x (FP32: residual and output)
-  float* s_vh = s_x + R;     // v, float pair
-  float* s_vl = s_vh + R;
-  int* s_rp = reinterpret_cast<int*>(s_vl + R);
+  RowArrays S;
+  S.sum = reinterpret_cast<float*>(smem);
+  S.yh = S.sum + R;
+  S.yl = S.yh + R;
+  S.x = S.yl + R;
+  S.vh = S.x + R;
+  S.vl = S.vh + R;
+  int* s_rp = reinterpret_cast<int*>(S.vl + R);
   int* s_heavy = s_rp + R + 4;
   int* s_ci = s_heavy + R;
-
-  __shared__ int s_nheavy;
-  __shared__ float s_rf[32];
-  __shared__ unsigned s_ru[32];
-  __shared__ double s_rd[3][32];
-  __shared__ unsigned long long s_rh[32];
-  __shared__ int s_decide;
-  __shared__ float s_last_r;
-  __shared__ unsigned s_last_n;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int b = blockIdx.x;
@@ -87,11 +63,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   if (tid == 0) s_nheavy = 0;
   for (int i = tid; i <= nr; i += blockDim.x) s_rp[i] = P.row_ptr[rb + i] - e0;
   for (int i = tid; i < nr; i += blockDim.x) {
-    s_vh[i] = P.v[rb + i];
-    s_vl[i] = P.vlo[rb + i];
-    s_yh[i] = P.y0[rb + i];
-    s_yl[i] = P.ylo[rb + i];
-    s_x[i] = P.x[rb + i];
+    S.vh[i] = P.v[rb + i];
+    S.vl[i] = P.vlo[rb + i];
+    S.yh[i] = P.y0[rb + i];
+    S.yl[i] = P.ylo[rb + i];
+    S.x[i] = P.x[rb + i];
   }
   __syncthreads();
   if (SMEM_CSR) {
@@ -100,9 +76,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   }
   for (int i = tid; i < nr; i += blockDim.x)
     if (s_rp[i + 1] - s_rp[i] > P.heavy) s_heavy[atomicAdd(&s_nheavy, 1)] = i;
+  set_gamma(P, P.k_start, T);
   __syncthreads();
   const int* __restrict__ ci = SMEM_CSR ? s_ci : (P.col_idx + e0);
   const int nheavy = s_nheavy;
+  const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
 
   unsigned long long hits = 0;
   int parity = 0, slot = 0, stop = 0;
@@ -111,8 +89,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   const int grp = tid / G, gl = tid & (G - 1), ngrp = blockDim.x / G;
 
   for (; k < P.k_end; ++k) {
-    const double gam_d = dev::gamma_at(P.gamma_mode, P.gamma0, P.gamma1, P.ramp, k);
-    const dev::f2 gam = dev::split_f64(gam_d);
+    const double gam_d = T.gd;
+    const dev::f2 gam = {T.gh, T.gl};
+    const float2 gnext = gamma_fetch(P, k + 1);
     const float* __restrict__ yin = parity ? P.y1 : P.y0;
     float* __restrict__ yout = parity ? P.y0 : P.y1;
 
@@ -130,7 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
       }
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (mine && gl == 0) s_sum[r] = acc;
+      if (mine && gl == 0) S.sum[r] = acc;
     }
     // ---- gather: heavy rows, a warp per row
     for (int h = warp; h < nheavy; h += nwarps) {
@@ -140,172 +119,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
       for (int e = a + lane; e < c; e += 32) acc += yin[ci[e]];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) s_sum[r] = acc;
+      if (lane == 0) S.sum[r] = acc;
     }
     __syncthreads();
 
-    // ---- update + check partials
+    // ---- update, stop-test partials, barrier, stop decision
     const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
-    float rmax = 0.0f;
-    unsigned nonbin = 0;
-    double l1 = 0.0, obj = 0.0, en = 0.0;
-    for (int i = tid; i < nr; i += blockDim.x) {
-      // the vertex's own state is a float pair; the neighbour sum is FP32 (what was gathered)
-      const dev::f2 y = {s_yh[i], s_yl[i]};
-      const dev::f2 v = {s_vh[i], s_vl[i]};
-      const float xo = s_x[i];
-      const float sn = s_sum[i];
-      // d = y + gamma s = (B y)_i
-      dev::f2 p = dev::two_prod(gam.hi, sn);
-      p.lo = __fmaf_rn(gam.lo, sn, p.lo);
-      dev::f2 d = dev::two_sum(y.hi, p.hi);
-      d = dev::fast_two_sum(d.hi, __fadd_rn(d.lo, __fadd_rn(y.lo, p.lo)));
-      dev::f2 xn, yn;
-      if (d.hi > kSafeDiv) {
-        xn = dev::div_f2(y, d);          // x' = y / (B y)
-        yn = dev::mul_f2(v, xn);         // y' = v x'
-      } else {
-        xn = {0.5f, 0.0f};               // safe division of the appendix module
-        yn = dev::mul_f2(v, xn);
-        ++hits;
-      }
-      s_yh[i] = yn.hi;
-      s_yl[i] = yn.lo;
-      s_x[i] = xn.hi;
-      yout[rb + i] = yn.hi;
-      if (check) {
-        const float dx = fabsf(xn.hi - xo);
-        rmax = fmaxf(rmax, dx);
-        l1 += (double)dx;
-        obj += (double)P.w[rb + i] * (double)xn.hi;
-        const double yd = (double)y.hi + (double)y.lo;
-        en += yd * (0.5 * ((double)d.hi + (double)d.lo) - ((double)v.hi + (double)v.lo));
-        nonbin += ((double)xn.hi > P.theta && (double)xn.hi < 1.0 - P.theta) ? 1u : 0u;
-      }
-    }
-    if (check) {
-      rmax = dev::warp_max(rmax);
-      nonbin = dev::warp_sum_u(nonbin);
-      l1 = dev::warp_sum_d(l1);
-      obj = dev::warp_sum_d(obj);
-      en = dev::warp_sum_d(en);
-      if (lane == 0) {
-        s_rf[warp] = rmax;
-        s_ru[warp] = nonbin;
-        s_rd[0][warp] = l1;
-        s_rd[1][warp] = obj;
-        s_rd[2][warp] = en;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        float r2 = lane < nwarps ? s_rf[lane] : 0.0f;
-        unsigned n2 = lane < nwarps ? s_ru[lane] : 0u;
-        double a2 = lane < nwarps ? s_rd[0][lane] : 0.0;
-        double o2 = lane < nwarps ? s_rd[1][lane] : 0.0;
-        double q2 = lane < nwarps ? s_rd[2][lane] : 0.0;
-        r2 = dev::warp_max(r2);
-        n2 = dev::warp_sum_u(n2);
-        a2 = dev::warp_sum_d(a2);
-        o2 = dev::warp_sum_d(o2);
-        q2 = dev::warp_sum_d(q2);
-        if (lane == 0) {
-          CheckPartial cp;
-          cp.rmax = r2;
-          cp.nonbin = n2;
-          cp.l1 = a2;
-          cp.obj = o2;
-          cp.energy = q2;
-          P.partials[slot * P.nblocks + b] = cp;
-        }
-      }
-    }
-
-    // ---- grid barrier (bounded)
-    ++nbar;
-    const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
-    if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit)) {
-      stop = 2;
+    CheckAcc acc;
+    update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
+    gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
+    if (check) write_check_partial(P, acc, slot, T);
+    stop = barrier_and_stop(P, nbar, slot, check, gam_d, k, T);
+    if (stop == 2) break;
+    parity ^= 1;
+    if (stop) {
+      ++k;
       break;
     }
-    parity ^= 1;
-
-    // ---- stop test: every CTA reduces the same partials in the same order
-    if (check) {
-      const CheckPartial* cps = P.partials + slot * P.nblocks;
-      float fr = 0.0f;
-      unsigned fn = 0;
-      for (int j = tid; j < P.nblocks; j += blockDim.x) {
-        fr = fmaxf(fr, __ldcg(&cps[j].rmax));
-        fn += __ldcg(&cps[j].nonbin);
-      }
-      fr = dev::warp_max(fr);
-      fn = dev::warp_sum_u(fn);
-      if (lane == 0) {
-        s_rf[warp] = fr;
-        s_ru[warp] = fn;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        float tr = 0.0f;
-        unsigned tn = 0;
-        for (int j = 0; j < nwarps; ++j) {
-          tr = fmaxf(tr, s_rf[j]);
-          tn += s_ru[j];
-        }
-        const bool bin_ok = (tn == 0u) && (gam_d * (1.0 - P.theta) > P.theta);
-        const bool res_ok = P.tol >= 0.0 && (double)tr <= P.tol;
-        s_decide = (bin_ok || res_ok) ? 1 : 0;
-        s_last_r = tr;
-        s_last_n = tn;
-      }
-      __syncthreads();
-      stop = s_decide;
-      if (b == 0 && (stop || k + 1 == P.k_end)) {
-        // FP64 summary of the final step, block 0 only, fixed order
-        double a2 = 0.0, o2 = 0.0, q2 = 0.0;
-        if (tid == 0) {
-          for (int j = 0; j < P.nblocks; ++j) {
-            a2 += __ldcg(&cps[j].l1);
-            o2 += __ldcg(&cps[j].obj);
-            q2 += __ldcg(&cps[j].energy);
-          }
-          P.info->resid_inf = s_last_r;
-          P.info->nonbin = s_last_n;
-          P.info->resid_l1 = a2;
-          P.info->objective = o2;
-          P.info->energy = q2;
-          P.info->binary = s_last_n == 0u;
-          P.info->converged = stop;
-        }
-      }
-      slot ^= 1;
-      __syncthreads();
-      if (stop) {
-        ++k;
-        break;
-      }
-    }
   }
-
   if (stop == 2) return;  // timeout: the status word says so; leave the state as is
+  finish_run(P, S, rb, nr, hits, k, parity, T);
+}
 
-  for (int i = tid; i < nr; i += blockDim.x) {
-    P.x[rb + i] = s_x[i];
-    P.ylo[rb + i] = s_yl[i];
-  }
-  // safe-division count
-  unsigned long long h = dev::warp_sum_ull(hits);
-  if (lane == 0) s_rh[warp] = h;
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long t = 0;
-    for (int j = 0; j < nwarps; ++j) t += s_rh[j];
-    if (t) atomicAdd(&P.info->hits, t);
-    if (b == 0) {
-      P.info->iters = k - P.k_start;
-      P.info->final_parity = parity;
-    }
-  }
+// gamma_k of Sec. 6 for k < len, in FP64 (the paper's ramp formula), split into float pairs
+__global__ void k_gamma_table(int len, int mode, double g0, double g1, int T, float2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= len) return;
+  const dev::f2 p = dev::split_f64(dev::gamma_at(mode, g0, g1, T, k));
+  out[k] = make_float2(p.hi, p.lo);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -351,10 +192,11 @@ __global__ void k_to_caller(int n, const float* __restrict__ x_int, const int32_
 
 using KernelFn = void (*)(const IterParams);
 
-static KernelFn pick_kernel(int G, bool smem_csr) {
-#define GN_PICK(g)                                                               \
-  case g:                                                                        \
-    return smem_csr ? (KernelFn)k_gn_persistent<g, true> : (KernelFn)k_gn_persistent<g, false>;
+static KernelFn pick_kernel(int G, int mode) {
+  const bool sm = mode == MODE_SMEM_CSR;
+#define GN_PICK(g) \
+  case g:          \
+    return sm ? (KernelFn)k_gn_persistent<g, true> : (KernelFn)k_gn_persistent<g, false>;
   switch (G) {
     GN_PICK(1)
     GN_PICK(2)
@@ -369,7 +211,7 @@ static KernelFn pick_kernel(int G, bool smem_csr) {
 
 static constexpr size_t kSmemLimit = 220 * 1024;
 
-gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp) {
+gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci) {
   const int n = g->n;
   const int64_t nnz = g->nnz;
   const int64_t alpha = 4;  // per-row cost in entry units (row bookkeeping + update)
@@ -403,19 +245,47 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp) {
   g->max_rows = max_rows;
   g->max_ents = max_ents;
   const int R = (max_rows + 3) & ~3;
-  const size_t base = sizeof(float) * 6 * (size_t)R + sizeof(int) * ((size_t)R + 4) + sizeof(int) * (size_t)R;
-  const size_t with_csr = base + sizeof(int) * (size_t)max_ents;
-  g->csr_in_smem = with_csr <= kSmemLimit;
-  g->smem_bytes = g->csr_in_smem ? with_csr : base;
-  if (g->smem_bytes > kSmemLimit)
-    return fail(GN_ERR_TOO_LARGE, "gn_create: a CTA's rows exceed shared memory (graph too large)");
-  g->threads = kThreads;
-  KernelFn fn = pick_kernel(G, g->csr_in_smem);
-  // the attribute is an upper bound shared by every graph that uses this instance
-  GN_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kSmemLimit));
+  const size_t rows_bytes = sizeof(float) * 6 * (size_t)R + sizeof(int) * ((size_t)R + 4) + sizeof(int) * (size_t)R;
+
+  const size_t csr_s = rows_bytes + 4 * (size_t)max_ents;
+  const int want = g->gather;
+  bool halo_fits = false;
+  if (want == GN_GATHER_AUTO || want == GN_GATHER_HALO) {
+    gn_status hst = build_halo(g, rp, ci, part, kSmemLimit, &halo_fits);
+    if (hst != GN_OK) return hst;
+    if (want == GN_GATHER_HALO && !halo_fits)
+      return fail(GN_ERR_TOO_LARGE, "gn_create: the halo gather mode does not fit shared memory");
+  }
+  KernelFn fn = nullptr;
   int per_sm = 0;
-  GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, g->smem_bytes));
+  if (halo_fits) {
+    g->mode = MODE_HALO;
+    g->gather = GN_GATHER_HALO;
+    const void* hk = halo_kernel(g->rows_pad_halo);
+    GN_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (KernelFn)hk, kThreads, g->smem_bytes));
+  } else {
+    if (want == GN_GATHER_SMEM_CSR && csr_s > kSmemLimit)
+      return fail(GN_ERR_TOO_LARGE, "gn_create: the CSR-in-shared-memory mode does not fit");
+    if (want != GN_GATHER_GLOBAL && csr_s <= kSmemLimit) {
+      g->mode = MODE_SMEM_CSR;
+      g->gather = GN_GATHER_SMEM_CSR;
+      g->smem_bytes = csr_s;
+    } else if (rows_bytes <= kSmemLimit) {
+      g->mode = MODE_GMEM;
+      g->gather = GN_GATHER_GLOBAL;
+      g->smem_bytes = rows_bytes;
+    } else {
+      return fail(GN_ERR_TOO_LARGE, "gn_create: a CTA's rows exceed shared memory (graph too large)");
+    }
+    fn = pick_kernel(G, g->mode);
+    // the attribute is an upper bound shared by every graph that uses this instance
+    GN_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemLimit));
+    GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, g->smem_bytes));
+  }
+  g->csr_in_smem = g->mode != MODE_GMEM;
+  g->threads = kThreads;
   if (per_sm < 1 || nb > per_sm * g->num_sms)
     return fail(GN_ERR_TOO_LARGE, "gn_create: persistent kernel does not fit co-resident");
   GN_CUDA(cudaMalloc(&g->d_part, sizeof(int32_t) * (nb + 1)));
@@ -461,6 +331,9 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.y1 = g->d_y[parity0 ^ 1];
   P.x = g->d_x;
   P.ylo = g->d_ylo;
+  P.hoff = g->d_hoff;
+  P.hblob = g->d_hblob;
+  P.halo_pad = g->halo_pad;
   P.partials = g->d_partials;
   P.bar = g->d_bar;
   P.status = &g->d_info->status;
@@ -477,10 +350,26 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.theta = p.theta_bin;
   P.tol = tol;
   P.heavy = g->heavy;
-  P.rows_pad = (g->max_rows + 3) & ~3;
+  P.rows_pad = g->mode == MODE_HALO ? g->rows_pad_halo : ((g->max_rows + 3) & ~3);
   P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
   P.unreachable = p.debug_unreachable_barrier ? 1 : 0;
-  KernelFn fn = pick_kernel(g->group, g->csr_in_smem);
+  // gamma table: one entry per iteration up to the end of the ramp (gamma is constant after)
+  const int glen = (p.gamma_mode == GN_GAMMA_FIXED || p.ramp_iters <= 1)
+                       ? 1
+                       : std::max(1, std::min(k_end, p.ramp_iters));
+  if (glen > g->gtab_cap) {
+    if (g->d_gtab) cudaFree(g->d_gtab);
+    g->d_gtab = nullptr;
+    g->gtab_cap = 0;
+    GN_CUDA(cudaMalloc(&g->d_gtab, sizeof(float2) * glen));
+    g->gtab_cap = glen;
+  }
+  k_gamma_table<<<(glen + 255) / 256, 256, 0, g->stream>>>(glen, p.gamma_mode, p.gamma0, p.gamma1,
+                                                           p.ramp_iters, (float2*)g->d_gtab);
+  GN_LAUNCHED();
+  P.gtab = (const float2*)g->d_gtab;
+  P.gtab_len = glen;
+  KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo) : pick_kernel(g->group, g->mode);
   GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned), g->stream));
   void* args[] = {(void*)&P};
   GN_CUDA(cudaEventRecord(g->ev0, g->stream));
@@ -623,10 +512,12 @@ static constexpr size_t kNaOffVlo = kNaOffV + kNaVec;
 static constexpr size_t kNaOffPartials = kNaOffVlo + kNaVec;
 static constexpr size_t kNaOffPart = kNaOffPartials + align256(sizeof(CheckPartial) * 2 * kNoAllocMaxCTAs);
 static constexpr size_t kNaOffInfo = kNaOffPart + align256(sizeof(int32_t) * (kNoAllocMaxCTAs + 1));
+static constexpr int kNoAllocMaxGamma = 16384;
 static constexpr size_t kNaOffBar = kNaOffInfo + align256(sizeof(DevInfo));
-static constexpr size_t kNoAllocScratchBytes = kNaOffBar + 256;
+static constexpr size_t kNaOffGtab = kNaOffBar + 256;
+static constexpr size_t kNoAllocScratchBytes = kNaOffGtab + align256(sizeof(float2) * kNoAllocMaxGamma);
 
-// the fixed scratch (about 1.3 MB per device)
+// the fixed scratch (about 1.5 MB per device)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // range, order and self-loop check of the caller's CSR (flags go to the run summary's status)
@@ -750,7 +641,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
       GN_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
       GN_CUDA(cudaDeviceGetAttribute(&g_na_sms[dev_id], cudaDevAttrMultiProcessorCount, dev_id));
       for (int G = 1; G <= 32; G <<= 1)
-        GN_CUDA(cudaFuncSetAttribute((const void*)pick_kernel(G, false),
+        GN_CUDA(cudaFuncSetAttribute((const void*)pick_kernel(G, MODE_GMEM),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
       g_na_ptr[dev_id] = static_cast<unsigned char*>(ptr);
     }
@@ -766,6 +657,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
   int32_t* s_part = reinterpret_cast<int32_t*>(base + kNaOffPart);
   DevInfo* s_info = reinterpret_cast<DevInfo*>(base + kNaOffInfo);
   unsigned* s_bar = reinterpret_cast<unsigned*>(base + kNaOffBar);
+  float2* s_gtab = reinterpret_cast<float2*>(base + kNaOffGtab);
 
   if (n == 0) {
     if (info) {
@@ -787,12 +679,17 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
   while (G < 32 && G * 3 < avg) G <<= 1;
   const int R = (rows_per + 3) & ~3;
   const size_t smem = sizeof(float) * 6 * (size_t)R + sizeof(int) * ((size_t)R + 4) + sizeof(int) * (size_t)R;
-  KernelFn fn = pick_kernel(G, false);
+  KernelFn fn = pick_kernel(G, MODE_GMEM);
   int per_sm = 0;
   GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
   if (per_sm < 1 || nb > per_sm * sms) return fail(GN_ERR_TOO_LARGE, "gn_run_noalloc: kernel does not fit");
   if ((int64_t)(max_iters - start_iter) * nb >= (int64_t)1 << 31)
     return fail(GN_ERR_TOO_LARGE, "gn_run_noalloc: too many iterations for one call");
+  const int glen = (p.gamma_mode == GN_GAMMA_FIXED || p.ramp_iters <= 1)
+                       ? 1
+                       : std::max(1, std::min(max_iters, p.ramp_iters));
+  if (glen > kNoAllocMaxGamma)
+    return fail(GN_ERR_TOO_LARGE, "gn_run_noalloc: the gamma ramp needs more than 16384 table entries");
 
   // what must start at zero: the run summary (status, counters) and the barrier counter
   GN_CUDA(cudaMemsetAsync(s_info, 0, sizeof(DevInfo), stream));
@@ -822,6 +719,14 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     P.y1 = s_y1;
     P.x = x_out;
     P.ylo = s_ylo;
+    P.hoff = nullptr;
+    P.hblob = nullptr;
+    P.halo_pad = 0;
+    k_gamma_table<<<(glen + 255) / 256, 256, 0, stream>>>(glen, p.gamma_mode, p.gamma0, p.gamma1,
+                                                          p.ramp_iters, s_gtab);
+    GN_LAUNCHED();
+    P.gtab = s_gtab;
+    P.gtab_len = glen;
     P.partials = s_partials;
     P.bar = s_bar;
     P.status = &s_info->status;

@@ -27,6 +27,8 @@ HOST, DEVICE = 0, 1
 GAMMA_PURSUIT, GAMMA_FIXED = 0, 1
 REORDER_NONE, REORDER_RCM, REORDER_DEGREE = 0, 1, 2
 KERNEL_AUTO, KERNEL_PERSISTENT, KERNEL_CTA = 0, 1, 2
+GATHER_AUTO, GATHER_GLOBAL, GATHER_SMEM_CSR, GATHER_HALO = 0, 1, 2, 3
+GATHER_NAMES = {1: "global", 2: "smem_csr", 3: "halo"}
 
 
 class GNError(RuntimeError):
@@ -41,6 +43,10 @@ class Params(ctypes.Structure):
                 ("theta_bin", ctypes.c_double), ("kernel", ctypes.c_int), ("record", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong), ("debug_unreachable_barrier", ctypes.c_int),
                 ("resume", ctypes.c_int)]
+
+
+class CreateOpts(ctypes.Structure):
+    _fields_ = [("reorder", ctypes.c_int), ("gather", ctypes.c_int)]
 
 
 class RunInfo(ctypes.Structure):
@@ -72,6 +78,13 @@ def lib():
         L.gn_default_params.restype = None
         L.gn_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, P, P, P, ctypes.c_int, ctypes.c_int, P]
         L.gn_create.restype = ctypes.c_int
+        L.gn_create_ex.argtypes = [ctypes.POINTER(P), ctypes.c_int32, P, P, P, ctypes.c_int,
+                                   ctypes.POINTER(CreateOpts), P]
+        L.gn_create_ex.restype = ctypes.c_int
+        L.gn_gather_mode.argtypes = [P]
+        L.gn_gather_mode.restype = ctypes.c_int
+        L.gn_kernel_launches.argtypes = []
+        L.gn_kernel_launches.restype = ctypes.c_int64
         L.gn_destroy.argtypes = [P]
         L.gn_destroy.restype = None
         L.gn_set_io.argtypes = [P, ctypes.c_int]
@@ -130,7 +143,7 @@ class Graph:
     """A graph resident on the GPU (gn_create).  Pass numpy arrays (host I/O mode) or CUDA
     tensors (device I/O mode, current stream)."""
 
-    def __init__(self, row_ptr, col_idx, w, reorder=REORDER_NONE, stream=None):
+    def __init__(self, row_ptr, col_idx, w, reorder=REORDER_NONE, stream=None, gather=GATHER_AUTO):
         self._h = P()
         self.device_io = _is_torch(row_ptr) and row_ptr.is_cuda
         if self.device_io:
@@ -148,10 +161,12 @@ class Graph:
             self.device = None
         self.n = int(row_ptr.shape[0]) - 1
         ci = col_idx if col_idx.shape[0] > 0 else None
-        st = lib().gn_create(ctypes.byref(self._h), self.n, _ptr(row_ptr), _ptr(ci), _ptr(w),
-                             DEVICE if self.device_io else HOST, int(reorder), st_ptr)
+        opts = CreateOpts(int(reorder), int(gather))
+        st = lib().gn_create_ex(ctypes.byref(self._h), self.n, _ptr(row_ptr), _ptr(ci), _ptr(w),
+                                DEVICE if self.device_io else HOST, ctypes.byref(opts), st_ptr)
         _check(st)
         self.nnz = int(lib().gn_num_entries(self._h))
+        self.gather = GATHER_NAMES.get(int(lib().gn_gather_mode(self._h)), "none")
 
     def close(self):
         if self._h:

@@ -29,14 +29,17 @@ def gn():
     return gnmod
 
 
-def dev_graph(gn, inst, reorder=0):
+def dev_graph(gn, inst, reorder=0, gather=0):
     import torch
     return gn.Graph(torch.from_numpy(inst.row_ptr).cuda(), torch.from_numpy(inst.col_idx).cuda(),
-                    torch.from_numpy(inst.w).cuda(), reorder=reorder)
+                    torch.from_numpy(inst.w).cuda(), reorder=reorder, gather=gather)
 
 
-def host_graph(gn, inst, reorder=0):
-    return gn.Graph(inst.row_ptr, inst.col_idx, inst.w, reorder=reorder)
+def host_graph(gn, inst, reorder=0, gather=0):
+    return gn.Graph(inst.row_ptr, inst.col_idx, inst.w, reorder=reorder, gather=gather)
+
+
+GATHERS = {"halo": 3, "smem_csr": 2, "global": 1}
 
 
 def to_np(x):
@@ -57,14 +60,16 @@ def fixed_steps(k, gamma_mode=0):
     return dict(max_iters=k, tol=-1.0), dict(theta_bin=-1.0, gamma_mode=gamma_mode, check_every=1)
 
 
+@pytest.mark.parametrize("gather", ["halo", "smem_csr", "global"])
 @pytest.mark.parametrize("k", [1, 5, 20])
 @pytest.mark.parametrize("which", ["er2000", "udg20k", "ba20k", "assign24"])
-def test_iterates_match_oracle(gn, which, k):
+def test_iterates_match_oracle(gn, which, k, gather):
     inst = {"er2000": lambda: inputs.workload_er_small(),
             "udg20k": lambda: inputs.unit_disk_graph(20000, 100000, 1240),
             "ba20k": lambda: inputs.ba_graph(20000, 5, 1241),
             "assign24": lambda: inputs.assignment_graph(24, 1242)}[which]()
-    g = dev_graph(gn, inst)
+    g = dev_graph(gn, inst, gather=GATHERS[gather])
+    assert g.gather == gather
     run_kw, pk = fixed_steps(k)
     x, info = g.run(params=gn.default_params(**pk), **run_kw)
     assert info["iters"] == k
@@ -85,11 +90,12 @@ def _tie_free(inst, p, max_iters=3000):
     return all(np.array_equal(sets[0], t) for t in sets[1:])
 
 
+@pytest.mark.parametrize("gather", ["halo", "global"])
 @pytest.mark.parametrize("seed", [1234, 1300, 1301, 1302])
-def test_final_set_matches_oracle_er2000(gn, seed):
+def test_final_set_matches_oracle_er2000(gn, seed, gather):
     inst = inputs.er_graph(2000, 10.0, seed)
     p = dict(check_every=10)
-    g = dev_graph(gn, inst)
+    g = dev_graph(gn, inst, gather=GATHERS[gather])
     x, info = g.run(max_iters=2000, tol=1e-7, params=gn.default_params(**p))
     xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=2000, tol=1e-7, p=oracle.params(**p))
     assert info["status"] == "OK" and io["status"] == "OK"
@@ -218,8 +224,9 @@ def test_barrier_timeout_returns_status(gn):
     assert info["status"] == "OK"
 
 
+@pytest.mark.parametrize("gather", ["halo", "global"])
 @pytest.mark.parametrize("case", ["empty", "edgeless", "k2", "star5000", "isolated_mix", "zero_iters"])
-def test_edge_cases(gn, case):
+def test_edge_cases(gn, case, gather):
     if case == "empty":
         inst = inputs.small_graph("E0", 0, [])
     elif case == "edgeless":
@@ -232,7 +239,7 @@ def test_edge_cases(gn, case):
     else:
         parts = [inputs.er_graph(700, 4, 1291), inputs.small_graph("iso", 50, []), inputs.ba_graph(900, 3, 1292)]
         inst = inputs.disjoint_union(parts)
-    g = host_graph(gn, inst)
+    g = host_graph(gn, inst, gather=GATHERS[gather])
     if case == "empty":
         x, info = g.run()
         assert x.size == 0

@@ -52,7 +52,8 @@ def _noalloc(torch, gn, L, inst, max_iters, tol, params):
 
 
 def _reference(gn, inst, max_iters, tol, params):
-    g = gn.Graph(inst.row_ptr, inst.col_idx, inst.w)
+    # the allocating entry point with the same gather mode (neighbour values through L1/L2)
+    g = gn.Graph(inst.row_ptr, inst.col_idx, inst.w, gather=gn.GATHER_GLOBAL)
     x, info = g.run(max_iters=max_iters, tol=tol, params=params)
     g.close()
     return x, info
