@@ -240,6 +240,78 @@ gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_i
                          const float* x0, int max_iters, double tol, const gn_params* p,
                          int start_iter, float* x_out, gn_run_info* info, void* stream);
 
+/* ==========================================================================================
+ * Batched GN: many independent instances in one persistent launch (one CTA per instance at a
+ * time from a work queue; each instance stops on its own stop test).  The iteration, schedule
+ * and stop test are gn_run's.  The run sequence is captured into a CUDA graph and replayed.
+ */
+#define GN_INSTANCE_CSR 0         /* a general simple graph given as CSR with local ids */
+#define GN_INSTANCE_ASSIGNMENT 1  /* the assignment conflict graph of a k x k matrix (Sec. 2: cells
+                                     (r, c) adjacent when they share a row or a column), n = k*k,
+                                     vertex r*k + c; no entries are passed: the neighbour sum is
+                                     the row sum plus the column sum minus twice the cell */
+
+typedef struct gn_batch gn_batch;
+
+typedef struct {
+  int iters;            /* iterations of this instance */
+  int status;           /* GN_OK, GN_WARN_NOT_BINARY or GN_WARN_NOT_CONVERGED */
+  int converged, binary;
+  double resid_inf;     /* at the last check */
+  double objective;     /* sum_i w_i x_i at the last check (float-pair sums, FP64 result) */
+  long long safe_div_hits;
+} gn_batch_info;
+
+/*
+ * gn_batch_create -- validate and upload `count` instances (each as in gn_create, n_i >= 1,
+ * n_i <= 16384; assignment instances k <= 128).
+ *   vtx_off  int64[count+1], prefix sums of n_i (w, x0, x_out, masks are concatenated by it)
+ *   ent_off  int64[count+1], prefix sums of the instances' CSR entries (0 for assignment ones)
+ *   row_ptr  int32[sum(n_i + 1)]: instance i's local row pointers start at vtx_off[i] + i
+ *            (values of assignment instances are ignored; NULL when every instance is one)
+ *   col_idx  int32[ent_off[count]] local neighbour ids (may be NULL when there are none)
+ *   w        float32[vtx_off[count]] weights, > 0
+ *   kind     int32[count] GN_INSTANCE_* (NULL = all CSR)
+ *   mem      GN_HOST or GN_DEVICE for every pointer of this and later batch calls
+ *   stream   cudaStream_t (NULL: the handle creates its own non-blocking stream)
+ * Errors as gn_create (GN_ERR_TOO_LARGE when an instance exceeds shared memory).
+ */
+gn_status gn_batch_create(gn_batch** b, int32_t count, const int64_t* vtx_off, const int64_t* ent_off,
+                          const int32_t* row_ptr, const int32_t* col_idx, const float* w,
+                          const int32_t* kind, int mem, void* stream);
+void gn_batch_destroy(gn_batch* b);
+
+/* gn_run for every instance: x0 float32[vtx_off[count]] or NULL (1/(deg+1)); x_out may be NULL;
+ * info gn_batch_info[count] may be NULL.  Returns the worst instance status (or an error). */
+gn_status gn_batch_run(gn_batch* b, const float* x0, int max_iters, double tol, const gn_params* p,
+                       float* x_out, gn_batch_info* info);
+
+/* Device time (ms) of the last gn_batch_run's captured sequence. */
+float gn_batch_last_ms(gn_batch* b);
+
+/* CTA size of the batch kernel (128, 256, 512 or 1024). */
+gn_status gn_batch_set_threads(gn_batch* b, int threads);
+
+/* Autotuner: times the batch kernel at each CTA size for max_iters iterations (twice each) and
+ * keeps the fastest; *threads_out receives it (may be NULL). */
+gn_status gn_batch_tune(gn_batch* b, const gn_params* p, int max_iters, int* threads_out);
+
+/* gn_extract_is for every instance of the last run: mask uint8[vtx_off[count]], counts int32[count],
+ * weights double[count] (FP64 W(S)), statuses int32[count]; any may be NULL.  Returns the worst
+ * status (GN_ERR_NOT_INDEPENDENT if any instance's set has an inner edge). */
+gn_status gn_batch_extract(gn_batch* b, uint8_t* mask, int32_t* counts, double* weights, int32_t* statuses);
+
+/*
+ * gn_random_start -- the random simplex start of the appendix module, for B starts at once:
+ * p = -log u, p <- p / max(p) (one maximum over all m = B*n draws, as the module divides by the
+ * maximum of the whole batch), x0 = clamp(p, 1e-3, 1).
+ *   m    number of values (B * n)
+ *   u    float32[m] DEVICE uniform draws in (0, 1] (the caller's generator)
+ *   x0   float32[m] DEVICE output (may alias u)
+ * Synchronous.  GN_ERR_ARG if a draw lies outside (0, 1].
+ */
+gn_status gn_random_start(int64_t m, const float* u, float* x0, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles,
  * all threads).  Lets a caller count the device work behind a sequence of calls. */
 int64_t gn_kernel_launches(void);

@@ -226,3 +226,12 @@ def hungarian(cost):
     assign = np.zeros(k, dtype=np.int32)
     total = _load().gno_hungarian(k, _p(c), _p(assign))
     return total, assign
+
+
+def random_start(u):
+    """The appendix module's random simplex start, FP64: p = -log u; p / max(p) over all draws;
+    clamp to [1e-3, 1].  (Pinned: exponential draws divided by their maximum lie in (0, 1], and
+    the clamp is the module's.)"""
+    p = -np.log(np.asarray(u, dtype=np.float64))
+    p = p / p.max()
+    return np.clip(p, 1e-3, 1.0)

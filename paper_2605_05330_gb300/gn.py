@@ -237,3 +237,181 @@ class Graph:
             dL_dxT = np.ascontiguousarray(dL_dxT, dtype=np.float32)
         _check(lib().gn_backward(self._h, _ptr(dL_dxT), _ptr(gw), _ptr(gx)))
         return (gw[: self.n] if gw is not None else None), (gx[: self.n] if gx is not None else None)
+
+
+# ------------------------------------------------------------------------------------------
+# batched GN
+
+INSTANCE_CSR, INSTANCE_ASSIGNMENT = 0, 1
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("converged", ctypes.c_int),
+                ("binary", ctypes.c_int), ("resid_inf", ctypes.c_double), ("objective", ctypes.c_double),
+                ("safe_div_hits", ctypes.c_longlong)]
+
+
+def _batch_lib():
+    L = lib()
+    if not hasattr(L, "_batch_ready"):
+        L.gn_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int32, P, P, P, P, P, P, ctypes.c_int, P]
+        L.gn_batch_create.restype = ctypes.c_int
+        L.gn_batch_destroy.argtypes = [P]
+        L.gn_batch_destroy.restype = None
+        L.gn_batch_run.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Params), P, P]
+        L.gn_batch_run.restype = ctypes.c_int
+        L.gn_batch_last_ms.argtypes = [P]
+        L.gn_batch_last_ms.restype = ctypes.c_float
+        L.gn_batch_set_threads.argtypes = [P, ctypes.c_int]
+        L.gn_batch_set_threads.restype = ctypes.c_int
+        L.gn_batch_tune.argtypes = [P, ctypes.POINTER(Params), ctypes.c_int, P]
+        L.gn_batch_tune.restype = ctypes.c_int
+        L.gn_batch_extract.argtypes = [P, P, P, P, P]
+        L.gn_batch_extract.restype = ctypes.c_int
+        L._batch_ready = True
+    return L
+
+
+def pack_batch(instances):
+    """Concatenates instances for gn_batch_create.  Each item is either a CSR instance (an
+    object with row_ptr, col_idx, w) or ("assignment", k, w) with w of length k*k."""
+    count = len(instances)
+    vtx = np.zeros(count + 1, np.int64)
+    ent = np.zeros(count + 1, np.int64)
+    kinds = np.zeros(max(count, 1), np.int32)
+    rps, cis, ws = [], [], []
+    for i, it in enumerate(instances):
+        if isinstance(it, tuple) and it[0] == "assignment":
+            k, w = it[1], np.asarray(it[2], np.float32)
+            n = k * k
+            kinds[i] = INSTANCE_ASSIGNMENT
+            rps.append(np.zeros(n + 1, np.int32))
+            ws.append(w)
+            e = 0
+        else:
+            n = len(it.row_ptr) - 1
+            rps.append(np.asarray(it.row_ptr, np.int32))
+            cis.append(np.asarray(it.col_idx, np.int32))
+            ws.append(np.asarray(it.w, np.float32))
+            e = int(it.row_ptr[-1])
+        vtx[i + 1] = vtx[i] + n
+        ent[i + 1] = ent[i] + e
+    rp = np.concatenate(rps) if rps else np.zeros(1, np.int32)
+    ci = np.concatenate(cis) if cis else np.zeros(1, np.int32)
+    w = np.concatenate(ws) if ws else np.zeros(1, np.float32)
+    return vtx, ent, rp, ci, w, kinds
+
+
+class Batch:
+    """Many instances in one persistent launch (gn_batch_*).  device=True keeps every array of
+    the calls on the GPU (torch tensors); otherwise numpy arrays (host I/O mode)."""
+
+    def __init__(self, instances, device=False):
+        L = _batch_lib()
+        self._h = P()
+        self.count = len(instances)
+        vtx, ent, rp, ci, w, kinds = pack_batch(instances)
+        self.vtx_off = vtx
+        self.device_io = device
+        if device:
+            import torch
+            self._keep = [torch.from_numpy(a).cuda() for a in (vtx, ent, rp, ci, w, kinds)]
+            args = [ctypes.c_void_p(t.data_ptr()) for t in self._keep]
+            stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        else:
+            self._keep = [vtx, ent, rp, ci, w, kinds]
+            args = [a.ctypes.data_as(P) for a in self._keep]
+            stream = None
+        _check(L.gn_batch_create(ctypes.byref(self._h), self.count, *args, DEVICE if device else HOST, stream))
+        self.ntot = int(vtx[-1])
+
+    def close(self):
+        if self._h:
+            _batch_lib().gn_batch_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _alloc(self, dtype, n):
+        if self.device_io:
+            import torch
+            tdt = {np.float32: torch.float32, np.uint8: torch.uint8, np.int32: torch.int32,
+                   np.float64: torch.float64}[dtype]
+            return torch.empty(max(n, 1), dtype=tdt, device="cuda")
+        return np.empty(max(n, 1), dtype=dtype)
+
+    def run(self, x0=None, max_iters=2000, tol=1e-7, params: Params | None = None, out=True):
+        p = params if params is not None else default_params()
+        x = self._alloc(np.float32, self.ntot) if out else None
+        info = (BatchInfo * max(self.count, 1))()
+        if x0 is not None and not self.device_io:
+            x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        st = _batch_lib().gn_batch_run(self._h, _ptr(x0), int(max_iters), float(tol), ctypes.byref(p), _ptr(x),
+                                       ctypes.cast(info, P))
+        _check(st)
+        infos = [{f: getattr(info[i], f) for f, _ in BatchInfo._fields_} for i in range(self.count)]
+        for d in infos:
+            d["status"] = STATUS[d["status"]]
+        return (x[: self.ntot] if x is not None else None), infos
+
+    @property
+    def last_ms(self):
+        return float(_batch_lib().gn_batch_last_ms(self._h))
+
+    def set_threads(self, t):
+        _check(_batch_lib().gn_batch_set_threads(self._h, int(t)))
+
+    def tune(self, params: Params | None = None, max_iters=200):
+        p = params if params is not None else default_params()
+        t = ctypes.c_int(0)
+        _check(_batch_lib().gn_batch_tune(self._h, ctypes.byref(p), int(max_iters), ctypes.cast(ctypes.pointer(t), P)))
+        return t.value
+
+    def extract(self):
+        mask = self._alloc(np.uint8, self.ntot)
+        counts = self._alloc(np.int32, self.count)
+        weights = self._alloc(np.float64, self.count)
+        statuses = self._alloc(np.int32, self.count)
+        st = _batch_lib().gn_batch_extract(self._h, _ptr(mask), _ptr(counts), _ptr(weights), _ptr(statuses))
+        if st < 0 and st != -7:
+            _check(st)
+        return STATUS[st], mask[: self.ntot], counts[: self.count], weights[: self.count], statuses[: self.count]
+
+
+def random_start(u):
+    """The appendix module's random simplex start from uniform draws u (CUDA tensor, any shape,
+    values in (0, 1]); returns x0 of the same shape (gn_random_start)."""
+    import torch
+    L = lib()
+    if not hasattr(L, "_start_ready"):
+        L.gn_random_start.argtypes = [ctypes.c_int64, P, P, P]
+        L.gn_random_start.restype = ctypes.c_int
+        L._start_ready = True
+    u = u.to(torch.float32).contiguous()
+    x0 = torch.empty_like(u)
+    _check(L.gn_random_start(u.numel(), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(x0.data_ptr()),
+                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return x0
+
+
+def multi_start(graph_inst, starts, seed, max_iters=2000, tol=1e-7, params: Params | None = None):
+    """The paper's random-start protocol on one graph: `starts` random simplex starts run as
+    one batch (copies of the graph as instances); returns the best start's (W(S), mask, info)
+    and the per-start weights."""
+    import torch
+    from . import inputs
+    n = graph_inst.n
+    u = torch.from_numpy(inputs.uniforms(starts * n, seed)).cuda()
+    x0 = random_start(u)
+    b = Batch([graph_inst] * starts, device=True)
+    x, infos = b.run(x0=x0, max_iters=max_iters, tol=tol, params=params)
+    st, mask, counts, weights, statuses = b.extract()
+    w = weights.cpu().numpy()
+    best = int(np.argmax(w))
+    m = mask.cpu().numpy()[best * n:(best + 1) * n]
+    b.close()
+    return float(w[best]), m, infos[best], w

@@ -264,6 +264,29 @@ def workload_batch(count: int = 4096, seed: int = SEED_BASE, k_hi: int = 64):
     return insts
 
 
+def batch_specs(count: int = 4096, seed: int = SEED_BASE, k_hi: int = 64):
+    """The batched workload without edge lists for the assignment instances: ER instances as
+    GraphInstance, assignment instances as ("assignment", k, w, cost) with w = 2 - cost."""
+    out = []
+    for i, (kind, size, deg) in enumerate(batch_sizes(count, seed, k_hi=k_hi)):
+        if kind == "er":
+            out.append(er_graph(size, deg, seed + 1 + i, name=f"b{i}_er{size}"))
+        else:
+            rng = rng_for(seed + 1 + i)
+            cost = rng.random((size, size))
+            w = (2.0 - cost).astype(np.float32).reshape(-1)
+            out.append(("assignment", size, w, (2.0 - w.astype(np.float64)).reshape(size, size)))
+    return out
+
+
+def assignment_instance(spec) -> GraphInstance:
+    """The CSR form of an ("assignment", k, w, cost) spec."""
+    _, k, w, cost = spec
+    rp, ci = rook_csr(k)
+    return GraphInstance(f"assign_k{k}", rp, ci, np.asarray(w, np.float32),
+                         {"kind": "assignment", "k": k, "cost": cost})
+
+
 def workload_diff(seed: int = SEED_BASE, n: int = 50_000, avg_deg: float = 12.0):
     """Differentiable workload: ER n=50,000 average degree 12, w ~ U[1,100], g ~ N(0,1)."""
     g = er_graph(n, avg_deg, seed, name=f"er_n{n}_d{avg_deg:g}")

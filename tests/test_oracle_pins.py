@@ -456,3 +456,15 @@ def test_zero_iterations_and_edgeless():
     empty = inputs.small_graph("E0", 0, [])
     x, info = oracle.run(empty.row_ptr, empty.col_idx, empty.w, max_iters=10)
     assert x.size == 0
+
+
+def test_random_start():
+    """Appendix module: exponential draws -log u scaled by their maximum and clamped to
+    [1e-3, 1]; the largest draw maps to exactly 1, tiny draws to the 1e-3 floor, and the
+    order of the draws is reversed (larger u, smaller p)."""
+    u = np.array([0.5, 0.25, 1.0 - 1e-12, 0.9999, 1e-6])
+    x = oracle.random_start(u)
+    assert x[4] == 1.0                                  # smallest u has the largest -log u
+    assert abs(x[0] - np.log(2) / np.log(1e6)) < 1e-15  # -log(1/2) / -log(1e-6)
+    assert x[2] == 1e-3 and x[3] == 1e-3                # clamped
+    assert np.all(np.diff(oracle.random_start(np.array([0.1, 0.2, 0.3, 0.4]))) < 0)
