@@ -33,6 +33,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -296,6 +298,79 @@ def form_multi_start(gn, torch, starts=16):
             "objective_gap_vs_sequential": float(max(abs(a - b) / a for a, b in zip(wseq, ws)))}
 
 
+def form_differentiable(gn, torch, reps=3):
+    """Differentiable GN on ER n=50,000 degree 12, T=200 unrolled steps, L = g . x_T: the library's
+    recorded forward + adjoint (sqrt(T) checkpoints) against (a) plain GN's forward for the same
+    200 steps and (b) torch autograd through the same unrolled iteration on the GPU (FP32)."""
+    from paper_2605_05330_gb300 import inputs
+    inst, gvec = inputs.workload_diff()
+    T = 200
+    dev = torch.device("cuda")
+    rp = torch.from_numpy(inst.row_ptr).to(dev)
+    ci = torch.from_numpy(inst.col_idx).to(dev)
+    wt = torch.from_numpy(inst.w).to(dev)
+    deg = torch.from_numpy(np.diff(inst.row_ptr).astype(np.float32)).to(dev)
+    x0 = 1.0 / (deg + 1.0)
+    gd = torch.from_numpy(gvec).to(dev)
+
+    def ours():
+        w = wt.clone().requires_grad_(True)
+        x = x0.clone().requires_grad_(True)
+        xT = gn.unrolled_gn(rp, ci, w, x, T)
+        L = torch.dot(gd, xT)
+        L.backward()
+        return L, w.grad, x.grad
+
+    rows = torch.repeat_interleave(torch.arange(inst.n, device=dev), rp[1:] - rp[:-1])
+    cols = ci.long()
+    gam = [float(t) * 1.5 + (1.0 - float(t)) * 0.9 for t in (np.arange(T) / 999.0)]
+
+    def autograd_ref():
+        w = wt.clone().requires_grad_(True)
+        x = x0.clone().requires_grad_(True)
+        v = torch.sqrt(w)
+        y = x
+        for g_ in gam:
+            nb = torch.zeros_like(y).index_add(0, rows, (v[cols] / v[rows]) * y[cols])
+            d = y + g_ * nb
+            ok = v * d > 1e-9
+            y = torch.where(ok, y / torch.where(ok, d, torch.ones_like(d)), torch.full_like(d, 0.5))
+        L = torch.dot(gd, y)
+        L.backward()
+        return L, w.grad, x.grad
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts), out
+
+    t_ours, (L1, gw1, gx1) = timed(ours)
+    t_ag, (L2, gw2, gx2) = timed(autograd_ref)
+    g = gn.Graph(rp, ci, wt)
+    p = gn.default_params(theta_bin=-1.0, check_every=T)
+
+    def plain():
+        return g.run(max_iters=T, tol=-1.0, params=p, out=False)
+    t_plain, (_, inf) = timed(plain)
+    obj_plain = inf["objective"]
+    g.close()
+    with torch.no_grad():
+        xr = gn.unrolled_gn(rp, ci, wt, x0, T)
+        obj_rec = float(torch.dot(wt.double(), xr.double()).item())
+    rel = lambda a, b: float(torch.linalg.norm(a.double() - b.double()) / torch.linalg.norm(b.double()))
+    return {"graph": inst.name, "T": T, "forward_backward_ms": 1000 * t_ours,
+            "plain_gn_forward_ms": 1000 * t_plain, "torch_autograd_gpu_ms": 1000 * t_ag,
+            "speedup_vs_torch_autograd": t_ag / t_ours, "cost_vs_plain_forward": t_ours / t_plain,
+            "grad_rel_diff_vs_torch_autograd": {"w": rel(gw1, gw2), "x0": rel(gx1, gx2)},
+            "objective_gap_vs_plain_gn": abs(obj_plain - obj_rec) / obj_plain}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -458,7 +533,8 @@ def main():
     forms = None
     if rank == 0 and not args.no_forms and not args.only:
         forms = {"batched": form_batched(gn, torch, args.steps, max(1, args.warmup)),
-                 "multi_start": form_multi_start(gn, torch)}
+                 "multi_start": form_multi_start(gn, torch),
+                 "differentiable": form_differentiable(gn, torch)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

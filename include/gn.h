@@ -76,7 +76,9 @@ typedef struct {
   int check_every;      /* stop-test cadence c >= 1 (default 10) */
   double theta_bin;     /* binarity threshold theta (default 1e-4) */
   int kernel;           /* GN_KERNEL_* (default AUTO) */
-  int record;           /* 1: keep sqrt(T) checkpoints of this run for gn_backward */
+  int record;           /* 1: differentiable run for gn_backward: exactly max_iters - start_iter
+                           steps (no stop test) through step kernels that keep a checkpoint
+                           every ceil(sqrt(T)) steps */
   long long spin_limit; /* device wait limit in polls (0 = default 1<<22) */
   int debug_unreachable_barrier; /* test hook: make the first grid barrier unreachable so
                                     that every CTA hits spin_limit; must be 0 in use */
@@ -195,13 +197,13 @@ gn_status gn_extract_is(gn_graph* g, const float* x, uint8_t* mask, int32_t* mem
 gn_status gn_objective(gn_graph* g, const float* x, double gamma, double* obj, double* energy);
 
 /*
- * gn_backward -- reverse mode of the last recorded gn_run (params.record = 1, gamma pursuit
- * or fixed, a fixed number of iterations: use tol < 0 and theta_bin < 0 so that the stop
- * test never fires).  Derived from the step's Jacobian (Lemma 1 of App. F, general form):
- * with s = (I + gamma A) y, the adjoint of y' = v (.) y / s is
+ * gn_backward -- reverse mode of the last recorded gn_run (params.record = 1: T fixed steps).
+ * Derived from the step's Jacobian (App. F, Lemma 1 in its general form): with s = (I + gamma A) y
+ * and x' = y / s, the adjoint of y' = v (.) x' is
  *   gbar_y = v (.) gbar' / s - (I + gamma A)(v (.) gbar' (.) y / s^2),
- *   gbar_v += gbar' (.) y / s.
- * Recomputation from sqrt(T) checkpoints.
+ *   gbar_v += gbar' (.) x',
+ * chained through y_0 = v (.) x_0, x_T = y_T / v and v = sqrt(w).  Each segment between
+ * checkpoints is recomputed, then reversed (two gathers per step).  Arithmetic is FP32.
  *   dL_dxT  float32[n] gradient of the loss w.r.t. the returned x (before the clamp, which
  *           is the identity on the iterates)
  *   dL_dw   float32[n] output, gradient w.r.t. w (may be NULL)

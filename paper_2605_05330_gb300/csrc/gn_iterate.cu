@@ -296,6 +296,8 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
   return GN_OK;
 }
 
+gn_status record_forward(gn_graph* g, int k_start, int k_end, const gn_params& p, DevInfo* out, float* ms);  // gn_adjoint.cu
+
 // gamma_k on the host, same arithmetic as the device (host code is built without FMA
 // contraction)
 double host_gamma(const gn_params& p, int k) {
@@ -421,7 +423,20 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
   int kused = GN_KERNEL_PERSISTENT;
   if ((int64_t)(max_iters - start_iter) * g->nblocks >= (int64_t)1 << 31)
     return fail(GN_ERR_TOO_LARGE, "gn_run: too many iterations for one call; split the run with start_iter");
-  if (max_iters > start_iter && g->n > 0) {
+  if (p.record && max_iters > start_iter && g->n > 0) {
+    // differentiable form: exactly max_iters - start_iter steps with sqrt(T) checkpoints
+    if (p.resume) return fail(GN_ERR_ARG, "gn_run: record and resume cannot be combined");
+    GN_CUDA(cudaMemcpyAsync(&di, g->d_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+    if (di.status == 0) {
+      st = record_forward(g, start_iter, max_iters, p, &di, &ms);
+      if (st != GN_OK) return st;
+      st = state_stats(g, g->d_x, p.theta_bin, &di.objective, &di.nonbin);
+      if (st != GN_OK) return st;
+      di.binary = di.nonbin == 0;
+      di.converged = di.binary && host_gamma(p, max_iters - 1) * (1.0 - p.theta_bin) > p.theta_bin;
+    }
+  } else if (max_iters > start_iter && g->n > 0) {
     st = run_iterations(g, start_iter, max_iters, tol, p, parity0, &di, &ms, &kused);
     if (st != GN_OK) return st;
     if (!(di.status & DEV_TIMEOUT)) g->state_parity = parity0 ^ di.final_parity;

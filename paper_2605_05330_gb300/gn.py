@@ -415,3 +415,47 @@ def multi_start(graph_inst, starts, seed, max_iters=2000, tol=1e-7, params: Para
     m = mask.cpu().numpy()[best * n:(best + 1) * n]
     b.close()
     return float(w[best]), m, infos[best], w
+
+
+# ------------------------------------------------------------------------------------------
+# differentiable GN
+
+def _grad_function():
+    import torch
+
+    class UnrolledGN(torch.autograd.Function):
+        """x_T of `iters` unrolled WRGN steps from x0 (gamma schedule of the params); the
+        backward is the library's adjoint (gn_backward) with sqrt(T) checkpointing."""
+
+        @staticmethod
+        def forward(ctx, row_ptr, col_idx, w, x0, iters, params, start_iter):
+            p = params if params is not None else default_params()
+            p = default_params(**{f: getattr(p, f) for f, _ in Params._fields_})
+            p.record = 1
+            g = Graph(row_ptr, col_idx, w.detach())
+            x, info = g.run(x0=x0.detach().contiguous(), max_iters=start_iter + iters, tol=-1.0, params=p,
+                            start_iter=start_iter)
+            ctx.graph = g
+            ctx.info = info
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            g = ctx.graph
+            dw, dx0 = g.backward(gx.contiguous().to(torch.float32))
+            g.close()
+            ctx.graph = None
+            return None, None, dw, dx0, None, None, None
+
+    return UnrolledGN
+
+
+_unrolled = None
+
+
+def unrolled_gn(row_ptr, col_idx, w, x0, iters, params: Params | None = None, start_iter=0):
+    """Differentiable GN on CUDA tensors: returns x_T (float32[n]); gradients flow to w and x0."""
+    global _unrolled
+    if _unrolled is None:
+        _unrolled = _grad_function()
+    return _unrolled.apply(row_ptr, col_idx, w, x0, int(iters), params, int(start_iter))

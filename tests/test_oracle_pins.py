@@ -468,3 +468,36 @@ def test_random_start():
     assert abs(x[0] - np.log(2) / np.log(1e6)) < 1e-15  # -log(1/2) / -log(1e-6)
     assert x[2] == 1e-3 and x[3] == 1e-3                # clamped
     assert np.all(np.diff(oracle.random_start(np.array([0.1, 0.2, 0.3, 0.4]))) < 0)
+
+
+@pytest.mark.parametrize("seed", [201, 202])
+def test_unrolled_gradient_against_central_differences(seed):
+    """The FP64 reference gradients of L = g . x_T (T unrolled WRGN steps) agree with central
+    finite differences of the forward in FP64 (w and x0 directions)."""
+    torch = pytest.importorskip("torch")
+    from oracle import grad
+    inst = inputs.er_graph(25, 4, seed)
+    rng = np.random.default_rng(seed)
+    x0 = rng.random(inst.n) + 0.1
+    g = rng.standard_normal(inst.n)
+    gam = grad.gammas(30)
+    w = inst.w.astype(np.float64)
+    L, dw, dx0, xT = grad.loss_and_grads(inst.row_ptr, inst.col_idx, w, x0, g, gam)
+
+    def f(wv, xv):
+        with torch.no_grad():
+            xt = grad.unrolled(inst.row_ptr, inst.col_idx, torch.tensor(wv), torch.tensor(xv), gam)
+        return float(np.dot(g, xt.numpy()))
+    # the forward equals the C oracle's iteration
+    xo, _ = oracle.run(inst.row_ptr, inst.col_idx, w, x0=x0, max_iters=30, tol=-1,
+                       p=oracle.params(theta_bin=-1.0))
+    np.testing.assert_allclose(xT, xo, rtol=1e-12, atol=1e-300)
+    for i in range(0, inst.n, 5):
+        h = 1e-6 * w[i]
+        e = np.zeros(inst.n); e[i] = h
+        fd = (f(w + e, x0) - f(w - e, x0)) / (2 * h)
+        assert abs(fd - dw[i]) <= 1e-6 * max(1.0, abs(dw[i]))
+        h = 1e-6 * x0[i]
+        e = np.zeros(inst.n); e[i] = h
+        fd = (f(w, x0 + e) - f(w, x0 - e)) / (2 * h)
+        assert abs(fd - dx0[i]) <= 1e-6 * max(1.0, abs(dx0[i]))
