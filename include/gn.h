@@ -314,6 +314,42 @@ gn_status gn_batch_extract(gn_batch* b, uint8_t* mask, int32_t* counts, double* 
  */
 gn_status gn_random_start(int64_t m, const float* u, float* x0, void* stream);
 
+/* ==========================================================================================
+ * Learned warm start (the paper's warm-start idea, Sec. 6, with a predictor learned from GN's
+ * own converged states; the network itself is not in the paper).  A 3-layer message-passing
+ * network, hidden width 64, FP32 master weights rounded to bf16 for every pass, FP32
+ * activations and accumulation:
+ *   f_i = [log w_i, log(1+deg_i), mean_{N(i)} log w_j, max_{N(i)} log w_j]
+ *   h^l_i = relu(W_s^l h^{l-1}_i + W_n^l mean_{j in N(i)} h^{l-1}_j + b^l)
+ *   p_i = sigmoid(w_o . h^3_i + b_o),  x0_i = clamp(p_i, 1e-3, 1)
+ *   loss = mean_i BCE(p_i, t_i) against a target state t (the rounded converged GN state).
+ * Parameters are one FP32 vector of gn_mpnn_num_params() values in the order
+ * [W_s^1 (64x4), W_n^1 (64x4), b^1, W_s^2 (64x64), W_n^2, b^2, W_s^3, W_n^3, b^3, w_o, b_o]
+ * (row-major, output index first).
+ */
+typedef struct gn_mpnn gn_mpnn;
+
+int gn_mpnn_num_params(void);
+/* init_params: float32[gn_mpnn_num_params()] HOST initial weights; stream for all work. */
+gn_status gn_mpnn_create(gn_mpnn** m, const float* init_params, void* stream);
+void gn_mpnn_destroy(gn_mpnn* m);
+/* Forward on a graph (its internal order): x0_out float32[n] DEVICE (caller order, may be NULL);
+ * target float32[n] DEVICE caller order in {0,1} or NULL (inference); *loss HOST (may be NULL).
+ * With a target, the activations are kept for gn_mpnn_backward. */
+gn_status gn_mpnn_forward(gn_mpnn* m, const gn_graph* g, float* x0_out, const float* target, double* loss);
+/* Inference: x0_out float32[n] DEVICE caller order = clamp((1/(deg+1))^(1-alpha) p^alpha, 1e-3, 1),
+ * the prediction blended geometrically with the cold start (alpha in [0, 1]; 1 = prediction only).
+ * Synchronous. */
+gn_status gn_mpnn_predict(gn_mpnn* m, const gn_graph* g, float alpha, float* x0_out);
+/* Adds the gradient of the last forward's loss to the gradient buffer (w.r.t. the bf16 weights). */
+gn_status gn_mpnn_backward(gn_mpnn* m, const gn_graph* g);
+gn_status gn_mpnn_zero_grad(gn_mpnn* m);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr; zeroes the gradients. */
+gn_status gn_mpnn_step(gn_mpnn* m, float lr);
+/* FP32 master weights / accumulated gradients to HOST float32[gn_mpnn_num_params()]. */
+gn_status gn_mpnn_get_params(gn_mpnn* m, float* out);
+gn_status gn_mpnn_get_grads(gn_mpnn* m, float* out);
+
 /* Number of CUDA kernels this library has launched in the process so far (all handles,
  * all threads).  Lets a caller count the device work behind a sequence of calls. */
 int64_t gn_kernel_launches(void);

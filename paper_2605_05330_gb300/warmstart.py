@@ -1,0 +1,183 @@
+"""Learned warm start for GN: a message-passing network predicts x0 from the graph and weights;
+it is trained on the GPU (the library's gn_mpnn_* kernels) on converged GN states that the
+method itself produces, and evaluated by iterations-to-binary and objective gap against the
+cold start 1/(deg+1).
+
+The paper warm-starts GN from fractional solutions of an external solver (Sec. 6); here the
+predictor is learned from GN's own cold-start outcomes, so a good prediction lets a shorter,
+steeper gamma schedule reach the same independent set in fewer iterations.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import gn, inputs
+
+P = ctypes.c_void_p
+
+
+def _lib():
+    L = gn.lib()
+    if not hasattr(L, "_mpnn_ready"):
+        L.gn_mpnn_num_params.argtypes = []
+        L.gn_mpnn_num_params.restype = ctypes.c_int
+        L.gn_mpnn_create.argtypes = [ctypes.POINTER(P), P, P]
+        L.gn_mpnn_create.restype = ctypes.c_int
+        L.gn_mpnn_destroy.argtypes = [P]
+        L.gn_mpnn_destroy.restype = None
+        L.gn_mpnn_forward.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_double)]
+        L.gn_mpnn_forward.restype = ctypes.c_int
+        L.gn_mpnn_predict.argtypes = [P, P, ctypes.c_float, P]
+        L.gn_mpnn_predict.restype = ctypes.c_int
+        L.gn_mpnn_backward.argtypes = [P, P]
+        L.gn_mpnn_backward.restype = ctypes.c_int
+        L.gn_mpnn_zero_grad.argtypes = [P]
+        L.gn_mpnn_zero_grad.restype = ctypes.c_int
+        L.gn_mpnn_step.argtypes = [P, ctypes.c_float]
+        L.gn_mpnn_step.restype = ctypes.c_int
+        L.gn_mpnn_get_params.argtypes = [P, P]
+        L.gn_mpnn_get_params.restype = ctypes.c_int
+        L.gn_mpnn_get_grads.argtypes = [P, P]
+        L.gn_mpnn_get_grads.restype = ctypes.c_int
+        L._mpnn_ready = True
+    return L
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """Glorot-uniform weights, zero biases, in the layout of gn_mpnn_num_params()."""
+    rng = np.random.default_rng(seed)
+    out = []
+    din = 4
+    for _ in range(3):
+        lim = math.sqrt(6.0 / (din + 64))
+        out.append(rng.uniform(-lim, lim, (64, din)))
+        out.append(rng.uniform(-lim, lim, (64, din)))
+        out.append(np.zeros(64))
+        din = 64
+    lim = math.sqrt(6.0 / 65)
+    out.append(rng.uniform(-lim, lim, 64))
+    out.append(np.zeros(1))
+    theta = np.concatenate([a.reshape(-1) for a in out]).astype(np.float32)
+    assert theta.size == _lib().gn_mpnn_num_params()
+    return theta
+
+
+class WarmStartNet:
+    def __init__(self, params: np.ndarray | None = None, seed: int = 0):
+        import torch
+        self._h = P()
+        theta = np.ascontiguousarray(params if params is not None else init_params(seed), np.float32)
+        gn._check(_lib().gn_mpnn_create(ctypes.byref(self._h), theta.ctypes.data_as(P),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def close(self):
+        if self._h:
+            _lib().gn_mpnn_destroy(self._h)
+            self._h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, graph: "gn.Graph", alpha: float = 1.0):
+        """x0 (CUDA tensor, caller order): the prediction blended geometrically with the cold
+        start, (1/(deg+1))^(1-alpha) p^alpha, clamped to [1e-3, 1]."""
+        import torch
+        x0 = torch.empty(graph.n, dtype=torch.float32, device="cuda")
+        gn._check(_lib().gn_mpnn_predict(self._h, graph._h, float(alpha), ctypes.c_void_p(x0.data_ptr())))
+        return x0
+
+    def loss_and_grad(self, graph: "gn.Graph", target) -> float:
+        """Forward with a target (CUDA float tensor, caller order) and backward; gradients are
+        accumulated until step()."""
+        loss = ctypes.c_double(0.0)
+        gn._check(_lib().gn_mpnn_forward(self._h, graph._h, None, ctypes.c_void_p(target.data_ptr()),
+                                         ctypes.byref(loss)))
+        gn._check(_lib().gn_mpnn_backward(self._h, graph._h))
+        return loss.value
+
+    def step(self, lr: float):
+        gn._check(_lib().gn_mpnn_step(self._h, float(lr)))
+
+    def zero_grad(self):
+        gn._check(_lib().gn_mpnn_zero_grad(self._h))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(_lib().gn_mpnn_num_params(), np.float32)
+        gn._check(_lib().gn_mpnn_get_params(self._h, out.ctypes.data_as(P)))
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(_lib().gn_mpnn_num_params(), np.float32)
+        gn._check(_lib().gn_mpnn_get_grads(self._h, out.ctypes.data_as(P)))
+        return out
+
+
+def training_graphs(count: int, seed: int = 9000, n_lo: int = 5000, n_hi: int = 50000, avg_deg: float = 10.0):
+    """Seeded unit-disk graphs with n uniform in [n_lo, n_hi] and the density of the 1M-edge
+    workload (average degree 10), lognormal weights."""
+    rng = inputs.rng_for(seed)
+    ns = rng.integers(n_lo, n_hi + 1, size=count)
+    return [inputs.unit_disk_graph(int(n), int(n * avg_deg / 2), seed + 1 + i, name=f"train{i}_udg{n}")
+            for i, n in enumerate(ns)]
+
+
+def device_graph(inst, reorder=gn.REORDER_RCM):
+    import torch
+    return gn.Graph(torch.from_numpy(inst.row_ptr).cuda(), torch.from_numpy(inst.col_idx).cuda(),
+                    torch.from_numpy(inst.w).cuda(), reorder=reorder)
+
+
+def label(graph: "gn.Graph"):
+    """The rounded converged state of a cold-start GN run (the training target)."""
+    x, info = graph.run(max_iters=2000, tol=1e-7)
+    return (x > 0.5).to(x.dtype), info
+
+
+def train(net: WarmStartNet, data, epochs: int = 8, lr: float = 3e-3, seed: int = 0):
+    """data: list of (graph, target).  One Adam step per graph per epoch (shuffled)."""
+    rng = np.random.default_rng(seed)
+    history = []
+    for ep in range(epochs):
+        losses = []
+        for i in rng.permutation(len(data)):
+            g, t = data[i]
+            losses.append(net.loss_and_grad(g, t))
+            net.step(lr)
+        history.append(float(np.mean(losses)))
+    return history
+
+
+def run_from(graph, x0, gamma0, ramp, max_iters=2000):
+    p = gn.default_params(gamma0=gamma0, ramp_iters=ramp)
+    x, info = graph.run(x0=x0, max_iters=max_iters, tol=1e-7, params=p)
+    W = graph.extract_is()[4]
+    return info, W
+
+
+SCHEDULES = ((0.9, 300), (0.95, 250), (1.0, 200), (1.0, 150), (1.05, 120), (1.1, 80))
+ALPHAS = (0.25, 0.5)
+
+
+def pick_schedule(net: WarmStartNet, graphs, gap_max=1e-3, alphas=ALPHAS, schedules=SCHEDULES):
+    """The (alpha, gamma0, ramp) with the fewest mean iterations-to-binary whose warm-started runs
+    stay within gap_max of the paper-schedule cold start on every validation graph (the graphs
+    the form is evaluated on are never used for the choice).  Returns None if no choice does."""
+    colds = [run_from(g, None, 0.9, 1000) for g in graphs]
+    best = None
+    for a in alphas:
+        x0s = [net.predict(g, a) for g in graphs]
+        for g0, T in schedules:
+            its, ok = [], True
+            for g, x0, (ci, Wc) in zip(graphs, x0s, colds):
+                info, W = run_from(g, x0, g0, T)
+                ok = ok and info["status"] == "OK" and (Wc - W) / Wc <= gap_max
+                its.append(info["iters"])
+            if ok and (best is None or np.mean(its) < best[3]):
+                best = (a, g0, T, float(np.mean(its)))
+    return best

@@ -501,3 +501,24 @@ def test_unrolled_gradient_against_central_differences(seed):
         e = np.zeros(inst.n); e[i] = h
         fd = (f(w, x0 + e) - f(w, x0 - e)) / (2 * h)
         assert abs(fd - dx0[i]) <= 1e-6 * max(1.0, abs(dx0[i]))
+
+
+def test_mpnn_reference_gradient_against_central_differences():
+    """The FP64 warm-start network's autograd gradient agrees with central differences of its
+    loss (FP64 weights, no bf16 rounding), on a small unit-disk graph."""
+    pytest.importorskip("torch")
+    from oracle import mpnn
+    inst = inputs.unit_disk_graph(60, 150, 301)
+    rng = np.random.default_rng(302)
+    theta = (rng.standard_normal(mpnn.num_params()) * 0.2).astype(np.float64)
+    t = (rng.random(inst.n) < 0.3).astype(np.float64)
+    p, loss, g = mpnn.forward(inst.row_ptr, inst.col_idx, inst.w, theta.astype(np.float32), t, bf16=False)
+    th32 = theta.astype(np.float32).astype(np.float64)
+    for idx in rng.choice(len(theta), 25, replace=False):
+        h = 1e-4
+        e = np.zeros(len(theta)); e[idx] = h
+        lp = mpnn.forward(inst.row_ptr, inst.col_idx, inst.w, th32 + e, t, bf16=False)[1]
+        lm = mpnn.forward(inst.row_ptr, inst.col_idx, inst.w, th32 - e, t, bf16=False)[1]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-5 * max(1.0, abs(g[idx])), (idx, fd, g[idx])
+    assert p.shape == (inst.n,) and np.all((p > 0) & (p < 1))
