@@ -23,7 +23,6 @@ from __future__ import annotations
 
 import argparse
 import ctypes
-import glob
 import hashlib
 import json
 import os
@@ -146,10 +145,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# the sources the iteration kernel is compiled from
+KERNEL_SOURCES = ("gn_halo.cu", "gn_iter_common.cuh", "gn_internal.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2605_05330_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2605_05330_gb300", "csrc", name), "rb").read())
     return h.hexdigest()
 
 
@@ -371,6 +374,61 @@ def form_differentiable(gn, torch, reps=3):
             "objective_gap_vs_plain_gn": abs(obj_plain - obj_rec) / obj_plain}
 
 
+def form_warm_start(gn, torch, graph, inst, reps=3):
+    """Learned warm start on the 1M-edge unit-disk graph: the message-passing network trained on
+    GN's converged states of 48 smaller unit-disk graphs (n in [5k, 50k], same density), blend and
+    schedule chosen on two validation graphs (n = 50k), then on the workload graph: iterations and
+    time to a binary state (network inference included) against the cold start with the paper's
+    schedule, and the cold start on the chosen schedule as the ablation."""
+    from paper_2605_05330_gb300 import inputs
+    from paper_2605_05330_gb300 import warmstart as ws
+    t0 = time.perf_counter()
+    data = []
+    for tr in ws.training_graphs(48, seed=9100, n_lo=5000, n_hi=50000):
+        g = ws.device_graph(tr)
+        t, _ = ws.label(g)
+        data.append((g, t))
+    net = ws.WarmStartNet(seed=7)
+    hist = ws.train(net, data, epochs=30, lr=3e-3)
+    for g, _ in data:
+        g.close()
+    vals = [ws.device_graph(inputs.unit_disk_graph(50000, 250000, s)) for s in (9201, 9203)]
+    best = ws.pick_schedule(net, vals)
+    for g in vals:
+        g.close()
+    train_s = time.perf_counter() - t0
+    if best is None:
+        net.close()
+        return {"graph": inst.name, "status": "no blend/schedule within 0.1% on the validation graphs"}
+    a, g0, T, _ = best
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t1)
+        return statistics.median(ts), out
+
+    t_cold, (ci, Wc) = timed(lambda: ws.run_from(graph, None, 0.9, 1000))
+    t_warm, (wi, Ww) = timed(lambda: ws.run_from(graph, net.predict(graph, a), g0, T))
+    t_pred, _ = timed(lambda: net.predict(graph, a))
+    _, (ai, Wa) = timed(lambda: ws.run_from(graph, None, g0, T))
+    net.close()
+    return {"graph": inst.name, "training": "48 unit-disk graphs n in [5k,50k], avg deg 10, 30 epochs, Adam 3e-3",
+            "training_s": train_s, "bce_first_last_epoch": [hist[0], hist[-1]],
+            "alpha": a, "schedule": {"gamma0": g0, "ramp_iters": T},
+            "cold_iters": ci["iters"], "warm_iters": wi["iters"], "cold_same_schedule_iters": ai["iters"],
+            "cold_time_to_binary_ms": 1000 * t_cold, "warm_time_to_binary_ms": 1000 * t_warm,
+            "network_inference_ms": 1000 * t_pred,
+            "speedup_vs_plain_gn": t_cold / t_warm,
+            "objective_gap": (Wc - Ww) / Wc, "objective_gap_cold_same_schedule": (Wc - Wa) / Wc,
+            "warm_status": wi["status"]}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -535,6 +593,9 @@ def main():
         forms = {"batched": form_batched(gn, torch, args.steps, max(1, args.warmup)),
                  "multi_start": form_multi_start(gn, torch),
                  "differentiable": form_differentiable(gn, torch)}
+        ui = [i for i, inst in enumerate(insts) if inst.meta["kind"] == "udg"]
+        if ui:
+            forms["warm_start"] = form_warm_start(gn, torch, graphs[ui[0]], insts[ui[0]])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -64,6 +64,12 @@ typedef enum {
 #define GN_REORDER_RCM 1        /* reverse Cuthill-McKee: locality of neighbour gathers */
 #define GN_REORDER_DEGREE 2     /* descending degree */
 
+#define GN_SYNC_AUTO 0          /* the grid barrier (GN_SYNC_GRID) */
+#define GN_SYNC_GRID 1          /* a grid-wide barrier after every iteration */
+#define GN_SYNC_NEIGHBOUR 2     /* halo mode: each CTA waits only for the CTAs whose rows it reads
+                                   (per-CTA completed-iteration flags); grid-wide only at the stop
+                                   test.  Same arithmetic, bit-identical results. */
+
 #define GN_KERNEL_AUTO 0
 #define GN_KERNEL_PERSISTENT 1  /* multi-CTA persistent kernel with a bounded grid barrier */
 #define GN_KERNEL_CTA 2         /* whole graph in one CTA's shared memory */
@@ -85,6 +91,7 @@ typedef struct {
   int resume;           /* 1: continue from the full-precision state the last gn_run left on the
                            handle (x0 ignored); with start_iter = that run's end this reproduces
                            an uninterrupted run bit for bit */
+  int sync;             /* GN_SYNC_* (default AUTO); other gather modes always use GRID */
 } gn_params;
 
 typedef struct {

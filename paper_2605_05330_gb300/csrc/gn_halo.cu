@@ -3,18 +3,38 @@
 // Each CTA owns a contiguous range of rows for the whole run and keeps everything it needs
 // in shared memory:
 //   s_all  = [ own weighted states y_i (hi parts) | external halo values | one zero ]
-//   a packed per-CTA block (built once on the host): the list of external neighbour ids,
-//   the light rows in SELL-32 slices (32 rows per slice, a lane per row, 16-bit local ids
-//   into s_all packed four per lane in 8-byte words, rows sorted interior-first then by
-//   degree, each column's entries spread over the shared-memory banks) and the heavy rows
-//   (a warp per row).
-// One iteration:
-//   1. cp.async copies of the external halo values y_j (written by other CTAs last iteration)
-//   2. row sums of the interior slices (only own rows: no wait) while the copies fly
-//   3. wait for the copies; row sums of the boundary slices and of the heavy rows
-//   4. the update (gn_iter_common.cuh), the stop-test partials, the bounded grid barrier
-// Only the distinct external neighbours of a CTA are read from L2 each iteration; every
-// other read is shared memory.
+//   a packed per-CTA block (built once on the host): the light rows in SELL-32 slices
+//   (32 rows per slice, a lane per row, 16-bit local ids into s_all packed four per lane in
+//   8-byte words, rows sorted interior-first then by degree, each column's entries spread
+//   over the shared-memory banks), the heavy rows cut into chunks of at most 256 entries
+//   (a warp per chunk; a row's chunk sums are added in chunk order, so the result does not
+//   depend on which warp took which chunk) and the CTA's send list.
+//
+// Halo exchange by inboxes.  Every CTA c has a contiguous inbox in global memory holding the
+// states of its external neighbours in the order of its halo (sorted by vertex id, so the
+// vertices of one owner CTA form one run).  After its update, each CTA writes its new states
+// into the runs it owns in the other CTAs' inboxes: the send list, pieces of at most 128
+// consecutive inbox slots, a warp per piece, so the stores are coalesced.  The next
+// iteration fetches the whole inbox with one bulk copy (cp.async.bulk, completion counted on
+// an mbarrier) while the interior rows are summed.  Two inbox buffers alternate.
+//
+// One iteration (r = k - k_start):
+//   1. bulk copy of inbox[r % 2] into the halo part of s_all
+//   2. row sums of the interior slices (only own rows: no wait) while the copy flies
+//   3. wait for the copy; row sums of the boundary slices and of the heavy-row chunks (one
+//      work list over the warps), then the heavy rows' chunk sums
+//   4. the update (gn_iter_common.cuh) and the stop-test partials
+//   5. the send list into inbox[(r + 1) % 2]
+//   6. the synchronisation: a bounded grid barrier, or (neighbour synchronisation) a release
+//      store of the CTA's completed-iteration count, with a grid-wide wait only at the stop
+//      test
+// A prologue writes the starting states into inbox[0].
+//
+// Neighbour synchronisation.  A CTA's inbox for iteration r is written by the CTAs owning its
+// halo (its dependency list) in iteration r - 1, so before step 1 warp 0 waits for those
+// CTAs' flags only.  The relation is symmetric (the graph is undirected), which also makes the
+// double-buffered inboxes safe: a CTA overwrites a buffer its dependents copied in iteration
+// r - 1 only after it has seen that they completed it.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -33,46 +53,111 @@ struct HaloHeader {
   int sell_len;    // SELL entries (with padding)
   int heavy_len;   // local ids of the heavy rows
   int zero_id;     // local id of the zero slot (padding)
-  int off_x;       // byte offsets of the sections from the block start
-  int off_meta;
+  int inbox_off;   // float offset of this CTA's inbox in one inbox buffer (multiple of 4)
+  int off_meta;    // byte offsets of the sections from the block start
   int off_srow;
   int off_sell;
   int off_hmeta;
   int off_hl;
   int bytes;       // block size (multiple of 16)
+  int ndep;        // CTAs owning external neighbours (the dependency list)
+  int off_dep;
+  int nchunk;      // heavy-row chunks
+  int off_hchunk;  // (entry offset into hl, count) per chunk
+  int off_hpart;   // float per chunk: its sum of this iteration
+  int npiece;      // send-list pieces
+  int off_piece;   // int4 per piece: (first inbox slot, length, first source, 0)
+  int off_src;     // uint16 per sent value: the own row it comes from
   int pad0, pad1;
 };
 
-static constexpr int kHeavyHalo = 64;  // rows with more entries go warp-per-row
+static constexpr int kHeavyHalo = 64;    // rows with more entries are cut into chunks
+static constexpr int kHeavyChunk = 256;  // entries per chunk (8 per lane)
+static constexpr int kSendPiece = 128;   // inbox slots per send piece
 
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// SELL-32 slices [s0, s1): warp per slice, lane per row.  A slice's width is a multiple of 4
-// and each lane's local ids come four at a time in one 8-byte word (layout [k/4][lane]).
-__device__ __forceinline__ void sum_slices(int s0, int s1, const int2* __restrict__ meta,
-                                           const short* __restrict__ srow,
-                                           const uint16_t* __restrict__ sell,
-                                           const float* __restrict__ s_all, float* __restrict__ s_sum) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int s = s0 + warp; s < s1; s += nwarps) {
-    const int2 m = meta[s];  // (entry offset, width): width % 4 == 0, offset % 128 == 0
-    const uint2* col = reinterpret_cast<const uint2*>(sell + m.x) + lane;
-    float a0 = 0.0f, a1 = 0.0f;
-    for (int q = 0; q < (m.y >> 2); ++q) {
-      const uint2 ids = col[q * 32];
-      a0 += s_all[ids.x & 0xffffu];
-      a1 += s_all[ids.x >> 16];
-      a0 += s_all[ids.y & 0xffffu];
-      a1 += s_all[ids.y >> 16];
-    }
-    const int r = srow[s * 32 + lane];
-    if (r >= 0) s_sum[r] = a0 + a1;
+// SELL-32 slice s: warp per slice, lane per row.  A slice's width is a multiple of 4 and each
+// lane's local ids come four at a time in one 8-byte word (layout [k/4][lane]).
+__device__ __forceinline__ void sum_slice(int s, const int2* __restrict__ meta, const short* __restrict__ srow,
+                                          const uint16_t* __restrict__ sell, const float* __restrict__ s_all,
+                                          float* __restrict__ s_sum) {
+  const int lane = threadIdx.x & 31;
+  const int2 m = meta[s];  // (entry offset, width): width % 4 == 0, offset % 128 == 0
+  const uint2* col = reinterpret_cast<const uint2*>(sell + m.x) + lane;
+  float a0 = 0.0f, a1 = 0.0f;
+  for (int q = 0; q < (m.y >> 2); ++q) {
+    const uint2 ids = col[q * 32];
+    a0 += s_all[ids.x & 0xffffu];
+    a1 += s_all[ids.x >> 16];
+    a0 += s_all[ids.y & 0xffffu];
+    a1 += s_all[ids.y >> 16];
   }
+  const int r = srow[s * 32 + lane];
+  if (r >= 0) s_sum[r] = a0 + a1;
+}
+
+// heavy-row chunk: entries [a, a + cnt) of hl, lane-strided with four independent sums, then
+// a butterfly over the warp (fixed order); lane 0 stores the chunk's sum
+__device__ __forceinline__ void sum_chunk(int2 ch, const uint16_t* __restrict__ hl,
+                                          const float* __restrict__ s_all, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+  int e = ch.x + lane;
+  const int end = ch.x + ch.y;
+  for (; e + 96 < end; e += 128) {
+    a0 += s_all[hl[e]];
+    a1 += s_all[hl[e + 32]];
+    a2 += s_all[hl[e + 64]];
+    a3 += s_all[hl[e + 96]];
+  }
+  for (; e < end; e += 32) a0 += s_all[hl[e]];
+  float acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) *out = acc;
+}
+
+// the send list: own states (s_all) into the other CTAs' inboxes, a warp per piece
+__device__ __forceinline__ void push_states(const int4* __restrict__ piece, int npiece,
+                                            const uint16_t* __restrict__ src, const float* __restrict__ s_all,
+                                            float* __restrict__ inbox) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int q = warp; q < npiece; q += nwarps) {
+    const int4 pc = piece[q];
+    for (int i = lane; i < pc.y; i += 32) inbox[pc.x + i] = s_all[src[pc.z + i]];
+  }
+}
+
+// ---- bulk copy with mbarrier completion (TMA, non-tensor form)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// thread 0: order the other CTAs' inbox writes (generic proxy, acquired at the last
+// synchronisation) before the async-proxy read of the copy, announce the bytes, start the
+// copy.  This CTA's own reads of the halo slots precede the copy through the bar.syncs since.
+__device__ __forceinline__ void bulk_fetch(float* s_dst, const float* g_src, unsigned bytes, uint64_t* bar) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  const unsigned d = (unsigned)__cvta_generic_to_shared(s_dst);
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(g_src), "r"(bytes), "r"(b)
+               : "memory");
+}
+// bounded wait for phase `parity` of the mbarrier; false if the limit was hit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit) {
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  for (long long i = 0; i <= limit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 // REG: a CTA owns at most 2 * kThreads rows and each thread keeps its (at most two) rows'
@@ -81,6 +166,8 @@ template <bool REG>
 __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TailShared T;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ int s_dep_ok;
   const int R = P.rows_pad;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const int b = blockIdx.x;
@@ -115,7 +202,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     for (int j = 0; j < 2; ++j) {
       const int i = tid + j * kThreads;
       const bool in = i < nr;
-      ry[j] = in ? dev::f2{P.y0[rb + i], P.ylo[rb + i]} : dev::f2{0.0f, 0.0f};
+      // a row past the CTA's end is a fixed point y = x = 1 (never a safe division)
+      ry[j] = in ? dev::f2{P.y0[rb + i], P.ylo[rb + i]} : dev::f2{1.0f, 0.0f};
       rv[j] = in ? dev::f2{P.v[rb + i], P.vlo[rb + i]} : dev::f2{1.0f, 0.0f};
       rx[j] = in ? P.x[rb + i] : 0.0f;
       rw[j] = in ? P.w[rb + i] : 0.0f;
@@ -130,70 +218,124 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       S.x[i] = P.x[rb + i];
     }
   }
+  if (tid == 0) mbar_init(&s_bar, 1);
   __syncthreads();
   const HaloHeader H = *reinterpret_cast<const HaloHeader*>(blk);
-  const int* __restrict__ xlist = reinterpret_cast<const int*>(blk + H.off_x);
   const int2* __restrict__ meta = reinterpret_cast<const int2*>(blk + H.off_meta);
   const short* __restrict__ srow = reinterpret_cast<const short*>(blk + H.off_srow);
   const uint16_t* __restrict__ sell = reinterpret_cast<const uint16_t*>(blk + H.off_sell);
   const int* __restrict__ hmeta = reinterpret_cast<const int*>(blk + H.off_hmeta);
   const uint16_t* __restrict__ hl = reinterpret_cast<const uint16_t*>(blk + H.off_hl);
+  const int* __restrict__ deps = reinterpret_cast<const int*>(blk + H.off_dep);
+  const int2* __restrict__ hchunk = reinterpret_cast<const int2*>(blk + H.off_hchunk);
+  float* __restrict__ hpart = reinterpret_cast<float*>(blk + H.off_hpart);
+  const int4* __restrict__ piece = reinterpret_cast<const int4*>(blk + H.off_piece);
+  const uint16_t* __restrict__ ssrc = reinterpret_cast<const uint16_t*>(blk + H.off_src);
   if (tid == 0) s_all[H.zero_id] = 0.0f;
   set_gamma(P, P.k_start, T);
   float* s_halo = s_all + R;
   const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
-  __syncthreads();
+  const unsigned halo_bytes = (unsigned)((H.lx + 3) & ~3) * 4u;
 
   unsigned long long hits = 0;
   int parity = 0, slot = 0, stop = 0;
   unsigned nbar = 0;
+  unsigned mphase = 0;  // parity of the mbarrier phase the next copy completes
   int k = P.k_start;
 
-  for (; k < P.k_end; ++k) {
+  // prologue: the starting states into inbox[0], then every CTA's inbox is complete
+  push_states(piece, H.npiece, ssrc, s_all, P.inbox);
+  if (P.iterflag) {
+    if (publish_and_stop(P, false, slot, false, 0.0, k - 1, T) == 2) stop = 2;
+  } else {
+    ++nbar;
+    if (!dev::grid_barrier(P.bar, nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u), P.status,
+                           P.spin_limit))
+      stop = 2;
+  }
+  // neighbour synchronisation: whether every CTA is known to have completed the pushes of
+  // iteration k - 1 (after a check); the first iteration waits for the prologue's pushes
+  bool synced = false;
+  bool fail = false;
+
+  for (; stop != 2 && k < P.k_end; ++k) {
+    const int r = k - P.k_start;
     const double gam_d = T.gd;
     const dev::f2 gam = {T.gh, T.gl};
     const float2 gnext = gamma_fetch(P, k + 1);
-    const float* __restrict__ yin = parity ? P.y1 : P.y0;
-    float* __restrict__ yout = parity ? P.y0 : P.y1;
+    const float* inbox_in = P.inbox + (size_t)(r & 1) * (size_t)P.inbox_len;
+    float* inbox_out = P.inbox + (size_t)((r + 1) & 1) * (size_t)P.inbox_len;
 
-    // 1. external halo values, asynchronously
-    for (int t = tid; t < H.lx; t += blockDim.x) cp_async4(&s_halo[t], yin + xlist[t]);
-    cp_async_commit();
+    // 0. neighbour synchronisation: the dependencies' iteration r - 1 (their pushes)
+    if (P.iterflag && !synced) {
+      if (warp == 0) {
+        const bool ok = dev::wait_flags_warp(P.iterflag, deps, H.ndep, (unsigned)r + 1u + (P.unreachable ? 1u : 0u),
+                                             P.status, P.spin_limit);
+        if (lane == 0) s_dep_ok = ok;
+      }
+      __syncthreads();
+      fail = !s_dep_ok;
+    }
+    // 1. the inbox, asynchronously
+    if (tid == 0 && H.lx > 0 && !fail) bulk_fetch(s_halo, inbox_in + H.inbox_off, halo_bytes, &s_bar);
     // 2. interior rows need only own values
-    sum_slices(0, H.ns_int, meta, srow, sell, s_all, S.sum);
-    // 3. boundary rows and heavy rows after the halo has landed
-    cp_async_wait_all();
-    __syncthreads();
-    sum_slices(H.ns_int, H.ns, meta, srow, sell, s_all, S.sum);
-    for (int h = warp; h < H.nheavy; h += nwarps) {
-      const int r = hmeta[3 * h], a = hmeta[3 * h + 1], c = a + hmeta[3 * h + 2];
-      float acc = 0.0f;
-      for (int e = a + lane; e < c; e += 32) acc += s_all[hl[e]];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) S.sum[r] = acc;
+    for (int s = warp; s < H.ns_int; s += nwarps) sum_slice(s, meta, srow, sell, s_all, S.sum);
+    // 3. boundary rows and heavy chunks after the inbox has landed
+    if (H.lx > 0 && !fail) {
+      if (!mbar_wait(&s_bar, mphase, P.spin_limit)) {
+        fail = true;
+        if (lane == 0) atomicOr(P.status, DEV_TIMEOUT);
+      }
+      mphase ^= 1u;
     }
     __syncthreads();
+    {
+      const int nsb = H.ns - H.ns_int;
+      for (int it = warp; it < nsb + H.nchunk; it += nwarps) {
+        if (it < nsb) sum_slice(H.ns_int + it, meta, srow, sell, s_all, S.sum);
+        else sum_chunk(hchunk[it - nsb], hl, s_all, hpart + (it - nsb));
+      }
+    }
+    __syncthreads();
+    if (H.nheavy) {  // CTA-uniform
+      for (int h = tid; h < H.nheavy; h += blockDim.x) {
+        const int rr = hmeta[3 * h], c0 = hmeta[3 * h + 1], nc = hmeta[3 * h + 2];
+        float acc = 0.0f;
+        for (int q = 0; q < nc; ++q) acc += hpart[c0 + q];
+        S.sum[rr] = acc;
+      }
+      __syncthreads();
+    }
 
-    // 4. update, stop-test partials, barrier, stop decision
+    // 4. update and stop-test partials
     const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
     CheckAcc acc;
     if (REG) {
+      // both rows unconditionally (no branch between them, so they interleave); a row past
+      // the end reads no sum, contributes no stop-test terms and stores nothing
+      bool in[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int i = tid + j * kThreads;
-        if (i < nr) {
-          update_one(ry[j], rv[j], rx[j], S.sum[i], gam, check, rw[j], th_lo, th_hi, hits, acc);
-          s_all[i] = ry[j].hi;
-          yout[rb + i] = ry[j].hi;
-        }
+        in[j] = i < nr;
+        update_one(ry[j], rv[j], rx[j], in[j] ? S.sum[i] : 0.0f, gam, check && in[j], rw[j], th_lo, th_hi, hits,
+                   acc);
       }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (in[j]) s_all[tid + j * kThreads] = ry[j].hi;
     } else {
-      update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
+      update_rows(S, nr, rb, P.w, nullptr, gam, check, th_lo, th_hi, hits, acc);
     }
-    gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
+    gamma_store(gnext, T);  // visible to every thread after the next __syncthreads
     if (check) write_check_partial(P, acc, slot, T);
-    stop = barrier_and_stop(P, nbar, slot, check, gam_d, k, T);
+    __syncthreads();
+    // 5. the new own states into the other CTAs' inboxes
+    push_states(piece, H.npiece, ssrc, s_all, inbox_out);
+    // 6. synchronisation and the stop decision
+    stop = P.iterflag ? publish_and_stop(P, fail, slot, check, gam_d, k, T)
+                      : barrier_and_stop(P, fail, nbar, slot, check, gam_d, k, T);
+    synced = check;
     if (stop == 2) break;
     parity ^= 1;
     if (stop) {
@@ -201,7 +343,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       break;
     }
   }
-  if (stop == 2) return;  // timeout: the status word says so; leave the state as is
+  if (stop == 2) {
+    // timeout: the status word says so.  A copy that this CTA started may still be in flight
+    // into shared memory: wait for it (bounded) before the CTA exits; leave the state as is.
+    if (fail && H.lx > 0) mbar_wait(&s_bar, mphase ^ 1u, P.spin_limit);
+    return;
+  }
+  float* yfin = parity ? P.y1 : P.y0;
   if (REG) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -209,15 +357,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       if (i < nr) {
         S.x[i] = rx[j];
         S.yl[i] = ry[j].lo;
+        yfin[rb + i] = ry[j].hi;
       }
     }
     __syncthreads();
+  } else {
+    for (int i = tid; i < nr; i += blockDim.x) yfin[rb + i] = S.yh[i];
   }
   finish_run(P, S, rb, nr, hits, k, parity, T);
 }
 
 // ------------------------------------------------------------------------------------------
-// host: the packed per-CTA blocks
+// host: the packed per-CTA blocks and the inboxes
 
 static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -231,27 +382,52 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   int max_rows = 0;
   for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
   const int R = (max_rows + 3) & ~3;
+  auto owner = [&](int j) { return (int)(std::upper_bound(part.begin(), part.end(), j) - part.begin()) - 1; };
+
+  // halos (sorted external neighbour ids) and inbox offsets
+  std::vector<std::vector<int32_t>> ext(nb);
+  std::vector<int64_t> inbox_off(nb + 1, 0);
+  {
+    std::vector<int32_t> stamp(std::max(n, 1), -1);
+    for (int b = 0; b < nb; ++b) {
+      const int rb = part[b], re = part[b + 1];
+      for (int64_t e = rp[rb]; e < rp[re]; ++e) {
+        const int j = ci[e];
+        if ((j < rb || j >= re) && stamp[j] != b) {
+          stamp[j] = b;
+          ext[b].push_back(j);
+        }
+      }
+      std::sort(ext[b].begin(), ext[b].end());
+      inbox_off[b + 1] = inbox_off[b] + (int64_t)((ext[b].size() + 3) & ~(size_t)3);
+    }
+  }
+  if (inbox_off[nb] > (int64_t)INT32_MAX) return GN_OK;  // does not fit 32-bit slots
+  // send lists: for each owner, the (inbox slot, own row) pairs in slot order.  Walking the
+  // consumers in order and each consumer's halo in order visits every owner's slots in
+  // increasing order, so each owner's list is sorted as built.
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
+  for (int c = 0; c < nb; ++c)
+    for (size_t t = 0; t < ext[c].size(); ++t) {
+      const int j = ext[c][t];
+      const int o = owner(j);
+      sends[o].push_back({(int32_t)(inbox_off[c] + (int64_t)t), j - part[o]});
+    }
 
   std::vector<std::vector<unsigned char>> blocks(nb);
-  std::vector<int32_t> stamp(std::max(n, 1), -1), extpos(std::max(n, 1), 0);
+  std::vector<int32_t> extpos(std::max(n, 1), 0);
   int lx_max = 0;
   size_t blk_max = 0;
   for (int b = 0; b < nb; ++b) {
     const int rb = part[b], re = part[b + 1], nr = re - rb;
-    // external halo: distinct neighbours outside [rb, re), sorted
-    std::vector<int32_t> ext;
-    for (int64_t e = rp[rb]; e < rp[re]; ++e) {
-      const int j = ci[e];
-      if ((j < rb || j >= re) && stamp[j] != b) {
-        stamp[j] = b;
-        ext.push_back(j);
-      }
+    const std::vector<int32_t>& xb = ext[b];
+    lx_max = std::max(lx_max, (int)xb.size());
+    // the CTAs owning the halo (xb is sorted, the partition is contiguous)
+    std::vector<int32_t> dep;
+    for (int j : xb) {
+      const int o = owner(j);
+      if (dep.empty() || dep.back() != o) dep.push_back(o);
     }
-    std::sort(ext.begin(), ext.end());
-    for (size_t t = 0; t < ext.size(); ++t) extpos[ext[t]] = (int32_t)t;
-    lx_max = std::max(lx_max, (int)ext.size());
-    blocks[b].clear();
-    // the local ids need the final halo padding; gather rows first, encode after
     std::vector<int> light_int, light_bnd, heavy;
     for (int r = 0; r < nr; ++r) {
       const int64_t a = rp[rb + r], c = rp[rb + r + 1];
@@ -274,13 +450,14 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
     std::vector<int> order(light_int.begin(), light_int.end());
     order.insert(order.end(), light_bnd.begin(), light_bnd.end());
     const int ns = ((int)order.size() + 31) / 32;
-    // store the structure as a plain vector of ints for encoding later
     HaloHeader H;
     memset(&H, 0, sizeof H);
     H.ns_int = ns_int;
     H.ns = ns;
     H.nheavy = (int)heavy.size();
-    H.lx = (int)ext.size();
+    H.lx = (int)xb.size();
+    H.ndep = (int)dep.size();
+    H.inbox_off = (int)inbox_off[b];
     std::vector<int2> meta(ns);
     std::vector<short> srow((size_t)ns * 32, (short)-1);
     int sell_len = 0;
@@ -298,20 +475,35 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
       meta[s] = make_int2(sell_len, wmax);
       sell_len += wmax * 32;
     }
+    // heavy rows: (row, first chunk, chunks); chunks: (entry offset into hl, count)
     int heavy_len = 0;
-    std::vector<int> hmeta;
+    std::vector<int> hmeta, hchunk;
     for (int r : heavy) {
       const int d = rp[rb + r + 1] - rp[rb + r];
       hmeta.push_back(r);
-      hmeta.push_back(heavy_len);
-      hmeta.push_back(d);
+      hmeta.push_back((int)hchunk.size() / 2);
+      hmeta.push_back((d + kHeavyChunk - 1) / kHeavyChunk);
+      for (int a = 0; a < d; a += kHeavyChunk) {
+        hchunk.push_back(heavy_len + a);
+        hchunk.push_back(std::min(kHeavyChunk, d - a));
+      }
       heavy_len += d;
     }
     H.sell_len = sell_len;
     H.heavy_len = heavy_len;
+    H.nchunk = (int)hchunk.size() / 2;
+    // send pieces: runs of consecutive inbox slots, at most kSendPiece long
+    const std::vector<std::pair<int32_t, int32_t>>& sd = sends[b];
+    std::vector<int4> pieces;
+    std::vector<uint16_t> src(sd.size());
+    for (size_t e = 0; e < sd.size(); ++e) {
+      src[e] = (uint16_t)sd[e].second;
+      if (pieces.empty() || pieces.back().y == kSendPiece || sd[e].first != pieces.back().x + pieces.back().y)
+        pieces.push_back(make_int4(sd[e].first, 0, (int)e, 0));
+      ++pieces.back().y;
+    }
+    H.npiece = (int)pieces.size();
     size_t off = align16(sizeof(HaloHeader));
-    H.off_x = (int)off;
-    off = align16(off + 4 * ext.size());
     H.off_meta = (int)off;
     off = align16(off + sizeof(int2) * ns);
     H.off_srow = (int)off;
@@ -322,18 +514,28 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
     off = align16(off + 4 * hmeta.size());
     H.off_hl = (int)off;
     off = align16(off + 2 * (size_t)heavy_len);
+    H.off_dep = (int)off;
+    off = align16(off + 4 * dep.size());
+    H.off_hchunk = (int)off;
+    off = align16(off + 4 * hchunk.size());
+    H.off_hpart = (int)off;
+    off = align16(off + 4 * (size_t)H.nchunk);
+    H.off_piece = (int)off;
+    off = align16(off + sizeof(int4) * pieces.size());
+    H.off_src = (int)off;
+    off = align16(off + 2 * src.size());
     H.bytes = (int)off;
     blk_max = std::max(blk_max, off);
     std::vector<unsigned char>& B = blocks[b];
     B.assign(off, 0);
     memcpy(B.data(), &H, sizeof H);
-    if (!ext.empty()) memcpy(B.data() + H.off_x, ext.data(), 4 * ext.size());
     if (ns) memcpy(B.data() + H.off_meta, meta.data(), sizeof(int2) * ns);
     if (ns) memcpy(B.data() + H.off_srow, srow.data(), sizeof(short) * 32 * (size_t)ns);
     if (!hmeta.empty()) memcpy(B.data() + H.off_hmeta, hmeta.data(), 4 * hmeta.size());
-    // local ids are encoded below, once the halo padding (and so the zero slot) is known;
-    // keep what the encoder needs
-    (void)order;
+    if (!dep.empty()) memcpy(B.data() + H.off_dep, dep.data(), 4 * dep.size());
+    if (!hchunk.empty()) memcpy(B.data() + H.off_hchunk, hchunk.data(), 4 * hchunk.size());
+    if (!pieces.empty()) memcpy(B.data() + H.off_piece, pieces.data(), sizeof(int4) * pieces.size());
+    if (!src.empty()) memcpy(B.data() + H.off_src, src.data(), 2 * src.size());
   }
   const int Lp = (lx_max + 3) & ~3;
   const int zero_id = R + Lp;
@@ -347,10 +549,7 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
     std::vector<unsigned char>& B = blocks[b];
     HaloHeader* H = reinterpret_cast<HaloHeader*>(B.data());
     H->zero_id = zero_id;
-    const int* ext = reinterpret_cast<const int*>(B.data() + H->off_x);
-    for (int t = 0; t < H->lx; ++t) {
-      extpos[ext[t]] = t;
-    }
+    for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = (int32_t)t;
     auto lid = [&](int j) -> uint16_t {
       return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
     };
@@ -387,9 +586,11 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
       }
     }
     const int* hm = reinterpret_cast<const int*>(B.data() + H->off_hmeta);
+    const int* hc = reinterpret_cast<const int*>(B.data() + H->off_hchunk);
     uint16_t* hl = reinterpret_cast<uint16_t*>(B.data() + H->off_hl);
     for (int h = 0; h < H->nheavy; ++h) {
-      const int r = hm[3 * h], o = hm[3 * h + 1], d = hm[3 * h + 2];
+      const int r = hm[3 * h], o = hc[2 * hm[3 * h + 1]];  // the row's entries start at its first chunk
+      const int d = rp[rb + r + 1] - rp[rb + r];
       for (int k = 0; k < d; ++k) hl[o + k] = lid(ci[rp[rb + r] + k]);
     }
   }
@@ -399,6 +600,9 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   for (int b = 0; b < nb; ++b) memcpy(blob.data() + hoff[b], blocks[b].data(), blocks[b].size());
   GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
   GN_CUDA(cudaMalloc(&g->d_hblob, blob.size()));
+  g->inbox_len = std::max<int64_t>(inbox_off[nb], 4);
+  GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 2 * (size_t)g->inbox_len));
+  GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 2 * (size_t)g->inbox_len, g->stream));
   GN_CUDA(cudaMemcpyAsync(g->d_hoff, hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaStreamSynchronize(g->stream));

@@ -118,6 +118,9 @@ struct gn_graph {
   double* d_bsum = nullptr;     // per-CTA FP64 partial sums of the small reductions
   gn::CheckPartial* d_partials = nullptr;  // [2][nblocks]
   unsigned* d_bar = nullptr;
+  unsigned* d_iterflag = nullptr;  // [kFlagStride * nblocks] per-CTA push counts (halo mode)
+  float* d_inbox = nullptr;        // [2][inbox_len] halo inboxes (halo mode)
+  int64_t inbox_len = 0;
   gn::DevInfo* d_info = nullptr;
   gn::DevInfo* h_info = nullptr;           // pinned
   int* d_flags = nullptr;
@@ -171,20 +174,26 @@ __device__ __forceinline__ int ld_relaxed_int(const int* p) {
 __device__ __forceinline__ void fence_acq_rel() {
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Grid-wide barrier for a cooperative launch (every CTA co-resident).  The counter only
 // grows: the e-th barrier of the launch waits for nblocks * (e + 1) arrivals.  The wait is
 // bounded: after `spin_limit` polls (or when another CTA has already reported a failure)
 // the CTA records DEV_TIMEOUT and returns false, so the kernel can wind down instead of
-// hanging.  Fence-fence synchronisation (release fence before the arrival, acquire fence
-// after the observed count) orders every write before the barrier with every read after it.
+// hanging.  The arrival is a release reduction (every write of the CTA before the barrier,
+// made visible to thread 0 by the bar.sync, is ordered before it); the polls are relaxed and
+// an acquire fence follows the observed count.
 __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target, int* status,
                                              long long spin_limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    fence_acq_rel();
-    atomicAdd(counter, 1u);
+    red_release_add(counter, 1u);
     int ok = 1;
     long long spins = 0;
     while (ld_relaxed(counter) < target) {
@@ -201,6 +210,37 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target,
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Per-CTA flags sit kFlagStride words apart (a cache line each), so the CTAs polling one flag
+// do not contend with those polling another.
+static constexpr int kFlagStride = 32;
+
+// One warp waits until flag ids[j] >= target for j < count (ids == nullptr: flag j), flag i
+// being flags[kFlagStride * i].
+// Relaxed polls (all of a lane's loads in flight together), then an acquire fence in every
+// lane, so the releases that set the flags are ordered before the warp's later reads; a
+// bar.sync after it extends that to the CTA.  Bounded like grid_barrier; warp-uniform result.
+__device__ __forceinline__ bool wait_flags_warp(const unsigned* flags, const int* ids, int count,
+                                                unsigned target, int* status, long long spin_limit) {
+  const int lane = threadIdx.x & 31;
+  long long spins = 0;
+  for (;;) {
+    bool ok = true;
+    for (int j = lane; j < count; j += 32) ok &= ld_relaxed(flags + kFlagStride * (ids ? ids[j] : j)) >= target;
+    if (__all_sync(0xffffffffu, ok)) break;
+    ++spins;
+    if ((spins & 255) == 0) {
+      const int bad = lane == 0 ? ld_relaxed_int(status) : 0;
+      if (__shfl_sync(0xffffffffu, bad, 0) != 0) return false;
+    }
+    if (spins > spin_limit) {
+      if (lane == 0) atomicOr(status, DEV_TIMEOUT);
+      return false;
+    }
+  }
+  fence_acq_rel();
+  return true;
 }
 
 __device__ __forceinline__ float warp_max(float v) {

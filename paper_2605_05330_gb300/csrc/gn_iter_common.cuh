@@ -41,6 +41,12 @@ struct IterParams {
   int halo_pad;
   long long spin_limit;
   int unreachable;
+  // halo mode: two inbox buffers of inbox_len floats (the per-CTA halo exchange)
+  float* inbox;
+  long long inbox_len;
+  // neighbour synchronisation (halo mode): iterflag[kFlagStride * b] counts the pushes CTA b
+  // has completed in this launch (zeroed before it); nullptr = a grid barrier every iteration
+  unsigned* iterflag;
 };
 
 static constexpr int kThreads = 1024;
@@ -67,6 +73,7 @@ struct CheckAcc {
 //   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. WRGN in the weighted state, App. B)
 //   d <= 1e-9: x' = 1/2 (the safe division of the appendix module)
 // and, at a check, its terms of the stop test (FP32 terms, summed as float pairs later).
+// Straight-line code (the safe division is a select), so a thread's rows can interleave.
 __device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x, float sn, dev::f2 gam,
                                            bool check, float wi, float th_lo, float th_hi,
                                            unsigned long long& hits, CheckAcc& acc) {
@@ -74,13 +81,10 @@ __device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x
   p.lo = dev::ffma(gam.lo, sn, p.lo);
   dev::f2 d = dev::two_sum(y.hi, p.hi);
   d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(y.lo, p.lo)));
-  dev::f2 xn;
-  if (d.hi > kSafeDiv) {
-    xn = dev::div_f2(y, d);
-  } else {
-    xn = {0.5f, 0.0f};
-    ++hits;
-  }
+  const bool ok = d.hi > kSafeDiv;
+  const dev::f2 q = dev::div_f2(y, ok ? d : dev::f2{1.0f, 0.0f});
+  const dev::f2 xn = ok ? q : dev::f2{0.5f, 0.0f};
+  hits += ok ? 0ull : 1ull;
   const dev::f2 yn = dev::mul_f2(v, xn);
   if (check) {
     const float dx = fabsf(xn.hi - x);
@@ -94,7 +98,8 @@ __device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x
   x = xn.hi;
 }
 
-// the update of rows [0, nr) of the CTA with their state in shared memory
+// the update of rows [0, nr) of the CTA with their state in shared memory (and, unless yout is
+// null, the new states to global memory)
 __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, const float* __restrict__ w,
                                             float* __restrict__ yout, dev::f2 gam, bool check,
                                             float th_lo, float th_hi, unsigned long long& hits,
@@ -107,7 +112,7 @@ __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, 
     S.yh[i] = y.hi;
     S.yl[i] = y.lo;
     S.x[i] = x;
-    yout[rb + i] = y.hi;
+    if (yout) yout[rb + i] = y.hi;
   }
 }
 
@@ -164,15 +169,10 @@ __device__ __forceinline__ void write_check_partial(const IterParams& P, const C
   }
 }
 
-// Grid barrier, then (at a check) the stop test: every CTA reduces the same partials in the
-// same order, so all take the same decision.  Returns 0 (continue), 1 (stop after this
-// iteration) or 2 (a wait hit its limit).
-__device__ __forceinline__ int barrier_and_stop(const IterParams& P, unsigned& nbar, int& slot, bool check,
-                                                double gam_d, int k, TailShared& T) {
-  ++nbar;
-  const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
-  if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit)) return 2;
-  if (!check) return 0;
+// The stop test after every CTA's partial of check slot `slot` is visible: every CTA reduces
+// the same partials in the same order, so all take the same decision.  Returns 0 (continue)
+// or 1 (stop after this iteration).
+__device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, double gam_d, int k, TailShared& T) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const CheckPartial* cps = P.partials + slot * P.nblocks;
   float fr = 0.0f;
@@ -219,6 +219,43 @@ __device__ __forceinline__ int barrier_and_stop(const IterParams& P, unsigned& n
   __syncthreads();
   slot ^= 1;
   return T.decide;
+}
+
+// Grid barrier, then (at a check) the stop test.  `fail` is this thread's record of a wait
+// that hit its limit earlier in the iteration.  Returns 0 (continue), 1 (stop after this
+// iteration) or 2 (a wait hit its limit).
+__device__ __forceinline__ int barrier_and_stop(const IterParams& P, bool fail, unsigned& nbar, int& slot,
+                                                bool check, double gam_d, int k, TailShared& T) {
+  if (__syncthreads_or(fail)) return 2;
+  ++nbar;
+  const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
+  if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit)) return 2;
+  if (!check) return 0;
+  return stop_decision(P, slot, gam_d, k, T);
+}
+
+// Neighbour synchronisation, end of iteration k (k = k_start - 1: the prologue): once every
+// thread's writes of the iteration (its pushed states, the check partial) are done, thread 0
+// publishes the CTA's count of completed pushes, k + 2 - k_start, with a release store.
+// Between checks nothing more: the next iteration's readers wait for the flags they need
+// (wait_flags_warp).  At a check the stop test needs every CTA's partial, so warp 0 waits for
+// all flags first.  `fail` is this thread's record of a wait that hit its limit earlier in the
+// iteration.  Returns 0, 1 or 2 like barrier_and_stop.
+__device__ __forceinline__ int publish_and_stop(const IterParams& P, bool fail, int& slot, bool check,
+                                                double gam_d, int k, TailShared& T) {
+  __shared__ int s_ok;
+  if (__syncthreads_or(fail)) return 2;
+  const unsigned done = (unsigned)(k + 2 - P.k_start);
+  if (threadIdx.x == 0) dev::st_release(P.iterflag + dev::kFlagStride * blockIdx.x, done);
+  if (!check) return 0;
+  if (threadIdx.x < 32) {
+    const bool ok = dev::wait_flags_warp(P.iterflag, nullptr, P.nblocks, done + (P.unreachable ? 1u : 0u),
+                                         P.status, P.spin_limit);
+    if (threadIdx.x == 0) s_ok = ok;
+  }
+  __syncthreads();
+  if (!s_ok) return 2;
+  return stop_decision(P, slot, gam_d, k, T);
 }
 
 // gamma_k (Sec. 6) for iteration k from the per-run table (float pair; FP64 value = hi + lo),

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
     update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
     gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
     if (check) write_check_partial(P, acc, slot, T);
-    stop = barrier_and_stop(P, nbar, slot, check, gam_d, k, T);
+    stop = barrier_and_stop(P, false, nbar, slot, check, gam_d, k, T);
     if (stop == 2) break;
     parity ^= 1;
     if (stop) {
@@ -210,14 +210,24 @@ static KernelFn pick_kernel(int G, int mode) {
 }
 
 static constexpr size_t kSmemLimit = 220 * 1024;
+static constexpr int64_t kHeavyRowCost = 64;  // the halo mode's heavy-row threshold
 
 gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci) {
   const int n = g->n;
   const int64_t nnz = g->nnz;
-  const int64_t alpha = 4;  // per-row cost in entry units (row bookkeeping + update)
-  const int64_t total = nnz + alpha * (int64_t)n;
+  // Per-row cost in entry units: its entries, plus alpha for the row bookkeeping and update.
+  // Entries of rows above kHeavyRowCost entries count twice: they are summed by whole warps
+  // from randomly placed neighbours (no bank-aware layout), at about half the rate.
+  const int64_t alpha = 4;
+  std::vector<int64_t> C((size_t)n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const int64_t d = rp[i + 1] - rp[i];
+    C[i + 1] = C[i] + d + (d > kHeavyRowCost ? d : 0) + alpha;
+  }
+  const int64_t total = C[n];
+  (void)nnz;
   int nb = (int)std::min<int64_t>(g->num_sms, std::max<int64_t>(1, (total + 2047) / 2048));
-  // balanced contiguous split of the prefix cost C(i) = rp[i] + alpha i
+  // balanced contiguous split of the prefix cost C
   std::vector<int32_t> part(nb + 1);
   part[0] = 0;
   for (int b = 1; b < nb; ++b) {
@@ -225,7 +235,7 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
     int lo = part[b - 1], hi = n;  // smallest i with C(i) >= want
     while (lo < hi) {
       int mid = lo + (hi - lo) / 2;
-      if ((int64_t)rp[mid] + alpha * mid >= want) hi = mid; else lo = mid + 1;
+      if (C[mid] >= want) hi = mid; else lo = mid + 1;
     }
     part[b] = lo;
   }
@@ -292,6 +302,7 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
   GN_CUDA(cudaMemcpyAsync(g->d_part, part.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice,
                           g->stream));
   GN_CUDA(cudaMalloc(&g->d_partials, sizeof(CheckPartial) * 2 * nb));
+  GN_CUDA(cudaMalloc(&g->d_iterflag, sizeof(unsigned) * dev::kFlagStride * nb));
   GN_CUDA(cudaStreamSynchronize(g->stream));
   return GN_OK;
 }
@@ -355,6 +366,9 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.rows_pad = g->mode == MODE_HALO ? g->rows_pad_halo : ((g->max_rows + 3) & ~3);
   P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
   P.unreachable = p.debug_unreachable_barrier ? 1 : 0;
+  P.iterflag = (g->mode == MODE_HALO && p.sync == GN_SYNC_NEIGHBOUR) ? g->d_iterflag : nullptr;
+  P.inbox = g->d_inbox;
+  P.inbox_len = g->inbox_len;
   // gamma table: one entry per iteration up to the end of the ramp (gamma is constant after)
   const int glen = (p.gamma_mode == GN_GAMMA_FIXED || p.ramp_iters <= 1)
                        ? 1
@@ -373,6 +387,8 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.gtab_len = glen;
   KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo) : pick_kernel(g->group, g->mode);
   GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned), g->stream));
+  if (P.iterflag)
+    GN_CUDA(cudaMemsetAsync(g->d_iterflag, 0, sizeof(unsigned) * dev::kFlagStride * g->nblocks, g->stream));
   void* args[] = {(void*)&P};
   GN_CUDA(cudaEventRecord(g->ev0, g->stream));
   GN_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(g->nblocks), dim3(g->threads), args,
@@ -399,7 +415,8 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
   if (start_iter < 0 || max_iters < start_iter || p.check_every < 1 || !(p.theta_bin < 0.5) ||
       !std::isfinite(p.gamma0) || !std::isfinite(p.gamma1) || p.gamma1 < 0 || p.gamma0 < 0 ||
       (p.gamma_mode != GN_GAMMA_PURSUIT && p.gamma_mode != GN_GAMMA_FIXED) ||
-      p.kernel < GN_KERNEL_AUTO || p.kernel > GN_KERNEL_CTA)
+      p.kernel < GN_KERNEL_AUTO || p.kernel > GN_KERNEL_CTA || p.sync < GN_SYNC_AUTO ||
+      p.sync > GN_SYNC_NEIGHBOUR)
     return fail(GN_ERR_ARG, "gn_run: bad argument");
   GN_CUDA(cudaSetDevice(g->device));
   GN_CUDA(cudaMemsetAsync(g->d_info, 0, sizeof(DevInfo), g->stream));
@@ -737,6 +754,9 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     P.hoff = nullptr;
     P.hblob = nullptr;
     P.halo_pad = 0;
+    P.iterflag = nullptr;
+    P.inbox = nullptr;
+    P.inbox_len = 0;
     k_gamma_table<<<(glen + 255) / 256, 256, 0, stream>>>(glen, p.gamma_mode, p.gamma0, p.gamma1,
                                                           p.ramp_iters, s_gtab);
     GN_LAUNCHED();

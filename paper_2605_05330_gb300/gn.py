@@ -27,6 +27,7 @@ HOST, DEVICE = 0, 1
 GAMMA_PURSUIT, GAMMA_FIXED = 0, 1
 REORDER_NONE, REORDER_RCM, REORDER_DEGREE = 0, 1, 2
 KERNEL_AUTO, KERNEL_PERSISTENT, KERNEL_CTA = 0, 1, 2
+SYNC_AUTO, SYNC_GRID, SYNC_NEIGHBOUR = 0, 1, 2
 GATHER_AUTO, GATHER_GLOBAL, GATHER_SMEM_CSR, GATHER_HALO = 0, 1, 2, 3
 GATHER_NAMES = {1: "global", 2: "smem_csr", 3: "halo"}
 
@@ -42,7 +43,7 @@ class Params(ctypes.Structure):
                 ("ramp_iters", ctypes.c_int), ("check_every", ctypes.c_int),
                 ("theta_bin", ctypes.c_double), ("kernel", ctypes.c_int), ("record", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong), ("debug_unreachable_barrier", ctypes.c_int),
-                ("resume", ctypes.c_int)]
+                ("resume", ctypes.c_int), ("sync", ctypes.c_int)]
 
 
 class CreateOpts(ctypes.Structure):

@@ -25,6 +25,10 @@ def gn():
     return gnmod
 
 
+# the benchmark's internal vertex order per graph
+REORDER = {"udg": 1, "ba": 0}
+
+
 @pytest.fixture(scope="module", params=["udg", "ba"])
 def workload(request):
     if request.param == "udg":
@@ -32,9 +36,15 @@ def workload(request):
     return inputs.workload_ba_1m()
 
 
+def bench_graph(gn, inst):
+    g = dev_graph(gn, inst, reorder=REORDER[inst.meta["kind"]])
+    assert g.gather == "halo"
+    return g
+
+
 def test_fullsize_iterates(gn, workload):
     inst = workload
-    g = dev_graph(gn, inst)
+    g = bench_graph(gn, inst)
     for k in (1, 10):
         run_kw, pk = fixed_steps(k)
         x, info = g.run(params=gn.default_params(**pk), **run_kw)
@@ -43,9 +53,22 @@ def test_fullsize_iterates(gn, workload):
         assert abs(info["objective"] - io["objective"]) <= 1e-6 * io["objective"]
 
 
+def test_fullsize_sync_modes_bit_identical(gn, workload):
+    """The complete run with neighbour synchronisation (the default on this path) and with a
+    grid barrier after every iteration: the same states bit for bit, the same stop."""
+    g = bench_graph(gn, workload)
+    out = []
+    for s in (gn.SYNC_NEIGHBOUR, gn.SYNC_GRID):
+        x, info = g.run(max_iters=2000, tol=1e-7, params=gn.default_params(sync=s))
+        out.append((to_np(x).copy(), info))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1]["iters"] == out[1][1]["iters"]
+    assert out[0][1]["objective"] == out[1][1]["objective"]
+
+
 def test_fullsize_run_to_binary(gn, workload):
     inst = workload
-    g = dev_graph(gn, inst)
+    g = bench_graph(gn, inst)
     x, info = g.run(max_iters=2000, tol=1e-7)
     assert info["status"] == "OK"
     st, mask, members, cnt, W = g.extract_is()
