@@ -135,7 +135,10 @@ gn_status gn_create(gn_graph** g, int32_t n, const int32_t* row_ptr, const int32
 #define GN_GATHER_AUTO 0      /* the fastest mode that fits (halo, else CSR in smem, else global) */
 #define GN_GATHER_GLOBAL 1    /* neighbour ids and values read through L1/L2 */
 #define GN_GATHER_SMEM_CSR 2  /* each CTA's neighbour ids in shared memory, values through L1/L2 */
-#define GN_GATHER_HALO 3      /* each CTA's distinct external neighbours staged in shared memory */
+#define GN_GATHER_HALO 3      /* each CTA's distinct external neighbours staged in shared memory,
+                                 exchanged by pull or push as the halo density suggests */
+#define GN_GATHER_HALO_PULL 4 /* halo mode, pull exchange (per-value gathers from the state vector) */
+#define GN_GATHER_HALO_PUSH 5 /* halo mode, push exchange (per-CTA inboxes fetched by bulk copy) */
 
 typedef struct {
   int reorder;          /* GN_REORDER_* */
@@ -148,6 +151,9 @@ gn_status gn_create_ex(gn_graph** g, int32_t n, const int32_t* row_ptr, const in
 
 /* Gather mode the handle's persistent kernel uses (GN_GATHER_GLOBAL, _SMEM_CSR or _HALO). */
 int gn_gather_mode(const gn_graph* g);
+
+/* Halo exchange of a GN_GATHER_HALO handle: 1 pull, 2 push; 0 for other modes or NULL. */
+int gn_halo_exchange(const gn_graph* g);
 
 /* Releases every resource of the handle (NULL is a no-op). */
 void gn_destroy(gn_graph* g);

@@ -226,6 +226,11 @@ extern "C" gn_status gn_create(gn_graph** out, int32_t n, const int32_t* row_ptr
 
 extern "C" int gn_gather_mode(const gn_graph* g) { return g ? g->gather : 0; }
 
+extern "C" int gn_halo_exchange(const gn_graph* g) {
+  if (!g || g->gather != GN_GATHER_HALO) return 0;
+  return g->halo_push ? 2 : 1;
+}
+
 extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_ptr,
                                   const int32_t* col_idx, const float* w, int mem,
                                   const gn_create_opts* opts, void* stream) {
@@ -233,7 +238,7 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
   const int reorder = opts ? opts->reorder : GN_REORDER_NONE;
   const int gather = opts ? opts->gather : GN_GATHER_AUTO;
   if (!out) return fail(GN_ERR_ARG, "gn_create: out is NULL");
-  if (gather < GN_GATHER_AUTO || gather > GN_GATHER_HALO) return fail(GN_ERR_ARG, "gn_create: bad gather mode");
+  if (gather < GN_GATHER_AUTO || gather > GN_GATHER_HALO_PUSH) return fail(GN_ERR_ARG, "gn_create: bad gather mode");
   *out = nullptr;
   if (n < 0 || !row_ptr || (!w && n > 0) || (mem != GN_HOST && mem != GN_DEVICE) ||
       reorder < GN_REORDER_NONE || reorder > GN_REORDER_DEGREE)

@@ -10,31 +10,38 @@
 //   (a warp per chunk; a row's chunk sums are added in chunk order, so the result does not
 //   depend on which warp took which chunk) and the CTA's send list.
 //
-// Halo exchange by inboxes.  Every CTA c has a contiguous inbox in global memory holding the
-// states of its external neighbours in the order of its halo (sorted by vertex id, so the
-// vertices of one owner CTA form one run).  After its update, each CTA writes its new states
-// into the runs it owns in the other CTAs' inboxes: the send list, pieces of at most 128
-// consecutive inbox slots, a warp per piece, so the stores are coalesced.  The next
-// iteration fetches the whole inbox with one bulk copy (cp.async.bulk, completion counted on
-// an mbarrier) while the interior rows are summed.  Two inbox buffers alternate.
+// Two ways to exchange the halo, chosen per graph when the blocks are built:
+//  * pull: each CTA writes its new states to the global state vector and, the next
+//    iteration, gathers its halo from there with one 4-byte cp.async per value (the block
+//    holds the list of external ids).  Cheap when a CTA's halo is dense in memory (a
+//    bandwidth-reducing order puts a CTA's external neighbours in a few long runs).
+//  * push, by inboxes: every CTA c has a contiguous inbox in global memory holding the
+//    states of its external neighbours in the order of its halo (sorted by vertex id, so the
+//    vertices of one owner CTA form one run).  After its update, each CTA writes its new
+//    states into the runs it owns in the other CTAs' inboxes: the send list, pieces of at
+//    most 128 consecutive inbox slots, a warp per piece, so the stores are coalesced.  The
+//    next iteration fetches the whole inbox with one bulk copy (cp.async.bulk, completion
+//    counted on an mbarrier).  Two inbox buffers alternate.  Pays off when halos are
+//    scattered (a few values per 32-byte sector), where per-value gathers are bound by the
+//    number of sectors each SM has in flight.
 //
 // One iteration (r = k - k_start):
-//   1. bulk copy of inbox[r % 2] into the halo part of s_all
-//   2. row sums of the interior slices (only own rows: no wait) while the copy flies
-//   3. wait for the copy; row sums of the boundary slices and of the heavy-row chunks (one
+//   1. the halo, asynchronously: pull cp.asyncs, or the bulk copy of inbox[r % 2]
+//   2. row sums of the interior slices (only own rows: no wait) while the halo flies
+//   3. wait for the halo; row sums of the boundary slices and of the heavy-row chunks (one
 //      work list over the warps), then the heavy rows' chunk sums
 //   4. the update (gn_iter_common.cuh) and the stop-test partials
-//   5. the send list into inbox[(r + 1) % 2]
+//   5. push: the send list into inbox[(r + 1) % 2]
 //   6. the synchronisation: a bounded grid barrier, or (neighbour synchronisation) a release
 //      store of the CTA's completed-iteration count, with a grid-wide wait only at the stop
 //      test
-// A prologue writes the starting states into inbox[0].
+// A prologue writes the starting states into inbox[0] (push).
 //
-// Neighbour synchronisation.  A CTA's inbox for iteration r is written by the CTAs owning its
-// halo (its dependency list) in iteration r - 1, so before step 1 warp 0 waits for those
-// CTAs' flags only.  The relation is symmetric (the graph is undirected), which also makes the
-// double-buffered inboxes safe: a CTA overwrites a buffer its dependents copied in iteration
-// r - 1 only after it has seen that they completed it.
+// Neighbour synchronisation.  A CTA's halo for iteration r is written by the CTAs owning it
+// (its dependency list) in iteration r - 1, so before step 1 warp 0 waits for those CTAs'
+// flags only.  The relation is symmetric (the graph is undirected), which also makes the
+// double buffers safe: a CTA overwrites a buffer its dependents read in iteration r - 1 only
+// after it has seen that they completed it.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -68,7 +75,8 @@ struct HaloHeader {
   int npiece;      // send-list pieces
   int off_piece;   // int4 per piece: (first inbox slot, length, first source, 0)
   int off_src;     // uint16 per sent value: the own row it comes from
-  int pad0, pad1;
+  int off_x;       // pull: int32 per halo value, its vertex id
+  int pad0;
 };
 
 static constexpr int kHeavyHalo = 64;    // rows with more entries are cut into chunks
@@ -116,14 +124,29 @@ __device__ __forceinline__ void sum_chunk(int2 ch, const uint16_t* __restrict__ 
   if (lane == 0) *out = acc;
 }
 
-// the send list: own states (s_all) into the other CTAs' inboxes, a warp per piece
+// pull: one halo value, global -> shared, asynchronously
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// push: the send list, own states (s_all) into the other CTAs' inboxes, a warp per piece of
+// at most 128 slots; each lane's (up to four) source reads are issued together
 __device__ __forceinline__ void push_states(const int4* __restrict__ piece, int npiece,
                                             const uint16_t* __restrict__ src, const float* __restrict__ s_all,
                                             float* __restrict__ inbox) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int q = warp; q < npiece; q += nwarps) {
     const int4 pc = piece[q];
-    for (int i = lane; i < pc.y; i += 32) inbox[pc.x + i] = s_all[src[pc.z + i]];
+    int id[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) id[u] = lane + 32 * u < pc.y ? src[pc.z + lane + 32 * u] : -1;
+    float val[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) val[u] = id[u] >= 0 ? s_all[id[u]] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (id[u] >= 0) inbox[pc.x + lane + 32 * u] = val[u];
   }
 }
 
@@ -162,7 +185,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long l
 
 // REG: a CTA owns at most 2 * kThreads rows and each thread keeps its (at most two) rows'
 // state in registers across iterations; only y (for the neighbour sums) goes to shared memory.
-template <bool REG>
+// PUSH: the halo exchange by inboxes, else pull.
+template <bool REG, bool PUSH>
 __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TailShared T;
@@ -231,6 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   float* __restrict__ hpart = reinterpret_cast<float*>(blk + H.off_hpart);
   const int4* __restrict__ piece = reinterpret_cast<const int4*>(blk + H.off_piece);
   const uint16_t* __restrict__ ssrc = reinterpret_cast<const uint16_t*>(blk + H.off_src);
+  const int* __restrict__ xlist = reinterpret_cast<const int*>(blk + H.off_x);
   if (tid == 0) s_all[H.zero_id] = 0.0f;
   set_gamma(P, P.k_start, T);
   float* s_halo = s_all + R;
@@ -243,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   unsigned mphase = 0;  // parity of the mbarrier phase the next copy completes
   int k = P.k_start;
 
-  // prologue: the starting states into inbox[0], then every CTA's inbox is complete
-  push_states(piece, H.npiece, ssrc, s_all, P.inbox);
+  // prologue: the starting states into inbox[0] (push), then every CTA's halo is complete
+  if (PUSH) push_states(piece, H.npiece, ssrc, s_all, P.inbox);
   if (P.iterflag) {
     if (publish_and_stop(P, false, slot, false, 0.0, k - 1, T) == 2) stop = 2;
   } else {
@@ -263,8 +288,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     const double gam_d = T.gd;
     const dev::f2 gam = {T.gh, T.gl};
     const float2 gnext = gamma_fetch(P, k + 1);
-    const float* inbox_in = P.inbox + (size_t)(r & 1) * (size_t)P.inbox_len;
-    float* inbox_out = P.inbox + (size_t)((r + 1) & 1) * (size_t)P.inbox_len;
+    const float* inbox_in = PUSH ? P.inbox + (size_t)(r & 1) * (size_t)P.inbox_len : nullptr;
+    float* inbox_out = PUSH ? P.inbox + (size_t)((r + 1) & 1) * (size_t)P.inbox_len : nullptr;
+    const float* __restrict__ yin = parity ? P.y1 : P.y0;  // pull
+    float* __restrict__ yout = parity ? P.y0 : P.y1;
 
     // 0. neighbour synchronisation: the dependencies' iteration r - 1 (their pushes)
     if (P.iterflag && !synced) {
@@ -276,25 +303,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       __syncthreads();
       fail = !s_dep_ok;
     }
-    // 1. the inbox, asynchronously
-    if (tid == 0 && H.lx > 0 && !fail) bulk_fetch(s_halo, inbox_in + H.inbox_off, halo_bytes, &s_bar);
+    // 1. the halo, asynchronously
+    if (PUSH) {
+      if (tid == 0 && H.lx > 0 && !fail) bulk_fetch(s_halo, inbox_in + H.inbox_off, halo_bytes, &s_bar);
+    } else {
+      for (int t = tid; t < H.lx; t += blockDim.x) cp_async4(&s_halo[t], yin + xlist[t]);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     // 2. interior rows need only own values
     for (int s = warp; s < H.ns_int; s += nwarps) sum_slice(s, meta, srow, sell, s_all, S.sum);
-    // 3. boundary rows and heavy chunks after the inbox has landed
-    if (H.lx > 0 && !fail) {
-      if (!mbar_wait(&s_bar, mphase, P.spin_limit)) {
-        fail = true;
-        if (lane == 0) atomicOr(P.status, DEV_TIMEOUT);
+    // 3. boundary rows and heavy chunks after the halo has landed
+    if (PUSH) {
+      if (H.lx > 0 && !fail) {
+        if (!mbar_wait(&s_bar, mphase, P.spin_limit)) {
+          fail = true;
+          if (lane == 0) atomicOr(P.status, DEV_TIMEOUT);
+        }
+        mphase ^= 1u;
       }
-      mphase ^= 1u;
+    } else {
+      asm volatile("cp.async.wait_all;" ::: "memory");
     }
     __syncthreads();
     {
+      // one round-robin over the warps of [boundary slices | heavy chunks], as two loops (a
+      // branch inside the slice loop costs the slices more than the split does)
       const int nsb = H.ns - H.ns_int;
-      for (int it = warp; it < nsb + H.nchunk; it += nwarps) {
-        if (it < nsb) sum_slice(H.ns_int + it, meta, srow, sell, s_all, S.sum);
-        else sum_chunk(hchunk[it - nsb], hl, s_all, hpart + (it - nsb));
-      }
+      for (int it = warp; it < nsb; it += nwarps) sum_slice(H.ns_int + it, meta, srow, sell, s_all, S.sum);
+      if (H.nchunk)  // CTA-uniform
+        for (int c = (warp - nsb % nwarps + nwarps) % nwarps; c < H.nchunk; c += nwarps)
+          sum_chunk(hchunk[c], hl, s_all, hpart + c);
     }
     __syncthreads();
     if (H.nheavy) {  // CTA-uniform
@@ -311,30 +349,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
     CheckAcc acc;
     if (REG) {
-      // both rows unconditionally (no branch between them, so they interleave); a row past
-      // the end reads no sum, contributes no stop-test terms and stores nothing
-      bool in[2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int i = tid + j * kThreads;
-        in[j] = i < nr;
-        update_one(ry[j], rv[j], rx[j], in[j] ? S.sum[i] : 0.0f, gam, check && in[j], rw[j], th_lo, th_hi, hits,
-                   acc);
+      // A warp with a second row somewhere computes both rows' arithmetic first (no branch
+      // between them, so they interleave), then the stop-test terms; a warp without one skips
+      // it (warp-uniform).  A row past the end reads no sum, adds no terms and stores nothing.
+      const bool in0 = tid < nr, in1 = tid + kThreads < nr;
+      RowStep s0;
+      if (__any_sync(0xffffffffu, in1)) {
+        s0 = update_core(ry[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
+        const RowStep s1 = update_core(ry[1], rv[1], in1 ? S.sum[tid + kThreads] : 0.0f, gam);
+        if (check && in1) check_terms(s1, ry[1], rv[1], rx[1], rw[1], th_lo, th_hi, acc);
+        hits += in1 && !s1.ok ? 1ull : 0ull;
+        ry[1] = s1.yn;
+        rx[1] = s1.xn.hi;
+        if (in1) {
+          s_all[tid + kThreads] = ry[1].hi;
+          if (!PUSH) yout[rb + tid + kThreads] = ry[1].hi;
+        }
+      } else {
+        s0 = update_core(ry[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
       }
-#pragma unroll
-      for (int j = 0; j < 2; ++j)
-        if (in[j]) s_all[tid + j * kThreads] = ry[j].hi;
+      if (check && in0) check_terms(s0, ry[0], rv[0], rx[0], rw[0], th_lo, th_hi, acc);
+      hits += in0 && !s0.ok ? 1ull : 0ull;
+      ry[0] = s0.yn;
+      rx[0] = s0.xn.hi;
+      if (in0) {
+        s_all[tid] = ry[0].hi;
+        if (!PUSH) yout[rb + tid] = ry[0].hi;
+      }
     } else {
-      update_rows(S, nr, rb, P.w, nullptr, gam, check, th_lo, th_hi, hits, acc);
+      update_rows(S, nr, rb, P.w, PUSH ? nullptr : yout, gam, check, th_lo, th_hi, hits, acc);
     }
     gamma_store(gnext, T);  // visible to every thread after the next __syncthreads
     if (check) write_check_partial(P, acc, slot, T);
-    __syncthreads();
     // 5. the new own states into the other CTAs' inboxes
-    push_states(piece, H.npiece, ssrc, s_all, inbox_out);
+    if (PUSH) {
+      __syncthreads();
+      push_states(piece, H.npiece, ssrc, s_all, inbox_out);
+    }
     // 6. synchronisation and the stop decision
     stop = P.iterflag ? publish_and_stop(P, fail, slot, check, gam_d, k, T)
-                      : barrier_and_stop(P, fail, nbar, slot, check, gam_d, k, T);
+                      : barrier_and_stop(P, PUSH, fail, nbar, slot, check, gam_d, k, T);
     synced = check;
     if (stop == 2) break;
     parity ^= 1;
@@ -346,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   if (stop == 2) {
     // timeout: the status word says so.  A copy that this CTA started may still be in flight
     // into shared memory: wait for it (bounded) before the CTA exits; leave the state as is.
-    if (fail && H.lx > 0) mbar_wait(&s_bar, mphase ^ 1u, P.spin_limit);
+    if (PUSH && fail && H.lx > 0) mbar_wait(&s_bar, mphase ^ 1u, P.spin_limit);
     return;
   }
   float* yfin = parity ? P.y1 : P.y0;
@@ -372,17 +426,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
 
 static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-// Builds the blocks for the partition `part`.  Returns false (and builds nothing on the
-// device) when a CTA's working set does not fit shared memory or 16-bit local ids.
+// A CTA's halo is "dense" when it averages at least this many values per 32-byte sector:
+// then the pull exchange reads few sectors and wins; below it the push exchange does.
+static constexpr double kPullDensity = 4.0;
+
+// Builds the blocks for the partition `part`, for the exchange `want` (GN_GATHER_HALO: by
+// the halo density; GN_GATHER_HALO_PULL / _PUSH: that one).  Sets *fits = false (and builds
+// nothing on the device) when a CTA's working set does not fit shared memory or 16-bit local
+// ids; with the automatic choice the other exchange is tried before giving up.
+static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
+                                   const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                                   const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits);
+
 gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
-                     const std::vector<int32_t>& part, size_t smem_limit, bool* fits) {
+                     const std::vector<int32_t>& part, size_t smem_limit, int want, bool* fits) {
   *fits = false;
   const int nb = (int)part.size() - 1;
   const int n = g->n;
-  int max_rows = 0;
-  for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
-  const int R = (max_rows + 3) & ~3;
-  auto owner = [&](int j) { return (int)(std::upper_bound(part.begin(), part.end(), j) - part.begin()) - 1; };
 
   // halos (sorted external neighbour ids) and inbox offsets
   std::vector<std::vector<int32_t>> ext(nb);
@@ -402,12 +462,42 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
       inbox_off[b + 1] = inbox_off[b] + (int64_t)((ext[b].size() + 3) & ~(size_t)3);
     }
   }
-  if (inbox_off[nb] > (int64_t)INT32_MAX) return GN_OK;  // does not fit 32-bit slots
+  // the exchange: forced, or by the density of the halos in memory
+  int64_t vals = 0, sectors = 0;
+  for (int b = 0; b < nb; ++b) {
+    vals += (int64_t)ext[b].size();
+    for (size_t t = 0; t < ext[b].size(); ++t) sectors += (t == 0 || ext[b][t] / 8 != ext[b][t - 1] / 8);
+  }
+  bool push = want == GN_GATHER_HALO_PUSH ||
+              (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
+  if (push && inbox_off[nb] > (int64_t)INT32_MAX) {  // inbox slots do not fit 32 bits
+    if (want == GN_GATHER_HALO_PUSH) return GN_OK;
+    push = false;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt, push = !push) {
+    if (attempt == 1 && want != GN_GATHER_HALO) break;
+    gn_status st = build_halo_blocks(g, rp, ci, part, ext, inbox_off, push, smem_limit, fits);
+    if (st != GN_OK || *fits) return st;
+  }
+  return GN_OK;
+}
+
+// The blocks for one exchange (see build_halo).
+static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
+                            const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                            const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits) {
+  *fits = false;
+  const int nb = (int)part.size() - 1;
+  const int n = g->n;
+  int max_rows = 0;
+  for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
+  const int R = (max_rows + 3) & ~3;
+  auto owner = [&](int j) { return (int)(std::upper_bound(part.begin(), part.end(), j) - part.begin()) - 1; };
   // send lists: for each owner, the (inbox slot, own row) pairs in slot order.  Walking the
   // consumers in order and each consumer's halo in order visits every owner's slots in
   // increasing order, so each owner's list is sorted as built.
   std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
-  for (int c = 0; c < nb; ++c)
+  for (int c = 0; push && c < nb; ++c)
     for (size_t t = 0; t < ext[c].size(); ++t) {
       const int j = ext[c][t];
       const int o = owner(j);
@@ -524,6 +614,8 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
     off = align16(off + sizeof(int4) * pieces.size());
     H.off_src = (int)off;
     off = align16(off + 2 * src.size());
+    H.off_x = (int)off;
+    if (!push) off = align16(off + 4 * xb.size());
     H.bytes = (int)off;
     blk_max = std::max(blk_max, off);
     std::vector<unsigned char>& B = blocks[b];
@@ -536,6 +628,7 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
     if (!hchunk.empty()) memcpy(B.data() + H.off_hchunk, hchunk.data(), 4 * hchunk.size());
     if (!pieces.empty()) memcpy(B.data() + H.off_piece, pieces.data(), sizeof(int4) * pieces.size());
     if (!src.empty()) memcpy(B.data() + H.off_src, src.data(), 2 * src.size());
+    if (!push && !xb.empty()) memcpy(B.data() + H.off_x, xb.data(), 4 * xb.size());
   }
   const int Lp = (lx_max + 3) & ~3;
   const int zero_id = R + Lp;
@@ -600,9 +693,12 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   for (int b = 0; b < nb; ++b) memcpy(blob.data() + hoff[b], blocks[b].data(), blocks[b].size());
   GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
   GN_CUDA(cudaMalloc(&g->d_hblob, blob.size()));
-  g->inbox_len = std::max<int64_t>(inbox_off[nb], 4);
-  GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 2 * (size_t)g->inbox_len));
-  GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 2 * (size_t)g->inbox_len, g->stream));
+  if (push) {
+    g->inbox_len = std::max<int64_t>(inbox_off[nb], 4);
+    GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 2 * (size_t)g->inbox_len));
+    GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 2 * (size_t)g->inbox_len, g->stream));
+  }
+  g->halo_push = push;
   GN_CUDA(cudaMemcpyAsync(g->d_hoff, hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaStreamSynchronize(g->stream));
@@ -613,8 +709,9 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   return GN_OK;
 }
 
-const void* halo_kernel(int rows_pad) {
-  return rows_pad <= 2 * kThreads ? (const void*)k_gn_halo<true> : (const void*)k_gn_halo<false>;
+const void* halo_kernel(int rows_pad, bool push) {
+  if (push) return rows_pad <= 2 * kThreads ? (const void*)k_gn_halo<true, true> : (const void*)k_gn_halo<false, true>;
+  return rows_pad <= 2 * kThreads ? (const void*)k_gn_halo<true, false> : (const void*)k_gn_halo<false, false>;
 }
 
 }  // namespace gn

@@ -119,7 +119,8 @@ struct gn_graph {
   gn::CheckPartial* d_partials = nullptr;  // [2][nblocks]
   unsigned* d_bar = nullptr;
   unsigned* d_iterflag = nullptr;  // [kFlagStride * nblocks] per-CTA push counts (halo mode)
-  float* d_inbox = nullptr;        // [2][inbox_len] halo inboxes (halo mode)
+  float* d_inbox = nullptr;        // [2][inbox_len] halo inboxes (halo mode, push exchange)
+  bool halo_push = false;          // halo mode: push exchange (else pull)
   int64_t inbox_len = 0;
   gn::DevInfo* d_info = nullptr;
   gn::DevInfo* h_info = nullptr;           // pinned
@@ -189,9 +190,15 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // made visible to thread 0 by the bar.sync, is ordered before it); the polls are relaxed and
 // an acquire fence follows the observed count.
 __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target, int* status,
-                                             long long spin_limit) {
+                                             long long spin_limit, bool may_fail = false, bool fail = false) {
   __shared__ int s_ok;
-  __syncthreads();
+  // `fail`: a thread's record of a wait that hit its limit earlier; the CTA then stops here.
+  // `may_fail` is a constant at the call site: without such waits a plain bar.sync does.
+  if (may_fail) {
+    if (__syncthreads_or(fail)) return false;
+  } else {
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     red_release_add(counter, 1u);
     int ok = 1;

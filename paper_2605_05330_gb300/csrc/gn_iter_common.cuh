@@ -69,33 +69,48 @@ struct CheckAcc {
   float l1 = 0.0f, obj = 0.0f, en = 0.0f;
 };
 
-// The update of one row (global id rb + i):
+// The update of one row (global id rb + i), arithmetic only:
 //   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. WRGN in the weighted state, App. B)
 //   d <= 1e-9: x' = 1/2 (the safe division of the appendix module)
-// and, at a check, its terms of the stop test (FP32 terms, summed as float pairs later).
 // Straight-line code (the safe division is a select), so a thread's rows can interleave.
-__device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x, float sn, dev::f2 gam,
-                                           bool check, float wi, float th_lo, float th_hi,
-                                           unsigned long long& hits, CheckAcc& acc) {
+struct RowStep {
+  dev::f2 xn, yn;  // new x and y
+  float d;         // (B y)_i, hi part (the energy term)
+  bool ok;         // false: the safe division fired
+};
+__device__ __forceinline__ RowStep update_core(const dev::f2 y, const dev::f2 v, float sn, dev::f2 gam) {
   dev::f2 p = dev::two_prod(gam.hi, sn);
   p.lo = dev::ffma(gam.lo, sn, p.lo);
   dev::f2 d = dev::two_sum(y.hi, p.hi);
   d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(y.lo, p.lo)));
-  const bool ok = d.hi > kSafeDiv;
-  const dev::f2 q = dev::div_f2(y, ok ? d : dev::f2{1.0f, 0.0f});
-  const dev::f2 xn = ok ? q : dev::f2{0.5f, 0.0f};
-  hits += ok ? 0ull : 1ull;
-  const dev::f2 yn = dev::mul_f2(v, xn);
-  if (check) {
-    const float dx = fabsf(xn.hi - x);
-    acc.rmax = fmaxf(acc.rmax, dx);
-    acc.l1 += dx;
-    acc.obj = __fmaf_rn(wi, xn.hi, acc.obj);
-    acc.en = __fmaf_rn(y.hi, __fmaf_rn(0.5f, d.hi, -v.hi), acc.en);
-    acc.nonbin += (xn.hi > th_lo && xn.hi < th_hi) ? 1u : 0u;
-  }
-  y = yn;
-  x = xn.hi;
+  RowStep r;
+  r.ok = d.hi > kSafeDiv;
+  const dev::f2 q = dev::div_f2(y, r.ok ? d : dev::f2{1.0f, 0.0f});
+  r.xn = r.ok ? q : dev::f2{0.5f, 0.0f};
+  r.yn = dev::mul_f2(v, r.xn);
+  r.d = d.hi;
+  return r;
+}
+// a row's terms of the stop test (FP32 terms, summed as float pairs later): y, v and x are
+// the values before the step
+__device__ __forceinline__ void check_terms(const RowStep& r, const dev::f2 y, const dev::f2 v, float x, float wi,
+                                            float th_lo, float th_hi, CheckAcc& acc) {
+  const float dx = fabsf(r.xn.hi - x);
+  acc.rmax = fmaxf(acc.rmax, dx);
+  acc.l1 += dx;
+  acc.obj = __fmaf_rn(wi, r.xn.hi, acc.obj);
+  acc.en = __fmaf_rn(y.hi, __fmaf_rn(0.5f, r.d, -v.hi), acc.en);
+  acc.nonbin += (r.xn.hi > th_lo && r.xn.hi < th_hi) ? 1u : 0u;
+}
+// the update of one row with, at a check, its stop-test terms
+__device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x, float sn, dev::f2 gam,
+                                           bool check, float wi, float th_lo, float th_hi,
+                                           unsigned long long& hits, CheckAcc& acc) {
+  const RowStep r = update_core(y, v, sn, gam);
+  hits += r.ok ? 0ull : 1ull;
+  if (check) check_terms(r, y, v, x, wi, th_lo, th_hi, acc);
+  y = r.yn;
+  x = r.xn.hi;
 }
 
 // the update of rows [0, nr) of the CTA with their state in shared memory (and, unless yout is
@@ -222,14 +237,14 @@ __device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, dou
 }
 
 // Grid barrier, then (at a check) the stop test.  `fail` is this thread's record of a wait
-// that hit its limit earlier in the iteration.  Returns 0 (continue), 1 (stop after this
-// iteration) or 2 (a wait hit its limit).
-__device__ __forceinline__ int barrier_and_stop(const IterParams& P, bool fail, unsigned& nbar, int& slot,
-                                                bool check, double gam_d, int k, TailShared& T) {
-  if (__syncthreads_or(fail)) return 2;
+// that hit its limit earlier in the iteration; `may_fail` (a constant at the call site) says
+// whether the kernel has such waits.  Returns 0 (continue), 1 (stop after this iteration) or 2
+// (a wait hit its limit).
+__device__ __forceinline__ int barrier_and_stop(const IterParams& P, bool may_fail, bool fail, unsigned& nbar,
+                                                int& slot, bool check, double gam_d, int k, TailShared& T) {
   ++nbar;
   const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
-  if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit)) return 2;
+  if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit, may_fail, fail)) return 2;
   if (!check) return 0;
   return stop_decision(P, slot, gam_d, k, T);
 }

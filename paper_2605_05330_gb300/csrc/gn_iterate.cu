@@ -30,8 +30,8 @@ enum GatherMode : int {
 };
 
 gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
-                     const std::vector<int32_t>& part, size_t smem_limit, bool* fits);  // gn_halo.cu
-const void* halo_kernel(int rows_pad);
+                     const std::vector<int32_t>& part, size_t smem_limit, int want, bool* fits);  // gn_halo.cu
+const void* halo_kernel(int rows_pad, bool push);
 
 // The generic persistent kernel: values gathered through L1/L2 (MODE_GMEM, MODE_SMEM_CSR),
 // G lanes per light row and a warp per heavy row.
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
     update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
     gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
     if (check) write_check_partial(P, acc, slot, T);
-    stop = barrier_and_stop(P, false, nbar, slot, check, gam_d, k, T);
+    stop = barrier_and_stop(P, false, false, nbar, slot, check, gam_d, k, T);
     if (stop == 2) break;
     parity ^= 1;
     if (stop) {
@@ -260,10 +260,12 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
   const size_t csr_s = rows_bytes + 4 * (size_t)max_ents;
   const int want = g->gather;
   bool halo_fits = false;
-  if (want == GN_GATHER_AUTO || want == GN_GATHER_HALO) {
-    gn_status hst = build_halo(g, rp, ci, part, kSmemLimit, &halo_fits);
+  const bool want_halo = want == GN_GATHER_HALO || want == GN_GATHER_HALO_PULL || want == GN_GATHER_HALO_PUSH;
+  if (want == GN_GATHER_AUTO || want_halo) {
+    gn_status hst = build_halo(g, rp, ci, part, kSmemLimit, want == GN_GATHER_AUTO ? GN_GATHER_HALO : want,
+                               &halo_fits);
     if (hst != GN_OK) return hst;
-    if (want == GN_GATHER_HALO && !halo_fits)
+    if (want_halo && !halo_fits)
       return fail(GN_ERR_TOO_LARGE, "gn_create: the halo gather mode does not fit shared memory");
   }
   KernelFn fn = nullptr;
@@ -271,7 +273,7 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
   if (halo_fits) {
     g->mode = MODE_HALO;
     g->gather = GN_GATHER_HALO;
-    const void* hk = halo_kernel(g->rows_pad_halo);
+    const void* hk = halo_kernel(g->rows_pad_halo, g->halo_push);
     GN_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
     GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (KernelFn)hk, kThreads, g->smem_bytes));
   } else {
@@ -385,7 +387,8 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   GN_LAUNCHED();
   P.gtab = (const float2*)g->d_gtab;
   P.gtab_len = glen;
-  KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo) : pick_kernel(g->group, g->mode);
+  KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo, g->halo_push)
+                                     : pick_kernel(g->group, g->mode);
   GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned), g->stream));
   if (P.iterflag)
     GN_CUDA(cudaMemsetAsync(g->d_iterflag, 0, sizeof(unsigned) * dev::kFlagStride * g->nblocks, g->stream));

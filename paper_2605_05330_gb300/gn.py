@@ -29,6 +29,8 @@ REORDER_NONE, REORDER_RCM, REORDER_DEGREE = 0, 1, 2
 KERNEL_AUTO, KERNEL_PERSISTENT, KERNEL_CTA = 0, 1, 2
 SYNC_AUTO, SYNC_GRID, SYNC_NEIGHBOUR = 0, 1, 2
 GATHER_AUTO, GATHER_GLOBAL, GATHER_SMEM_CSR, GATHER_HALO = 0, 1, 2, 3
+GATHER_HALO_PULL, GATHER_HALO_PUSH = 4, 5
+EXCHANGE_NAMES = {0: "none", 1: "pull", 2: "push"}
 GATHER_NAMES = {1: "global", 2: "smem_csr", 3: "halo"}
 
 
@@ -84,6 +86,8 @@ def lib():
         L.gn_create_ex.restype = ctypes.c_int
         L.gn_gather_mode.argtypes = [P]
         L.gn_gather_mode.restype = ctypes.c_int
+        L.gn_halo_exchange.argtypes = [P]
+        L.gn_halo_exchange.restype = ctypes.c_int
         L.gn_kernel_launches.argtypes = []
         L.gn_kernel_launches.restype = ctypes.c_int64
         L.gn_destroy.argtypes = [P]
@@ -168,6 +172,7 @@ class Graph:
         _check(st)
         self.nnz = int(lib().gn_num_entries(self._h))
         self.gather = GATHER_NAMES.get(int(lib().gn_gather_mode(self._h)), "none")
+        self.exchange = EXCHANGE_NAMES[int(lib().gn_halo_exchange(self._h))]
 
     def close(self):
         if self._h:

@@ -53,6 +53,22 @@ def test_fullsize_iterates(gn, workload):
         assert abs(info["objective"] - io["objective"]) <= 1e-6 * io["objective"]
 
 
+def test_fullsize_exchange_choice_and_bit_identity(gn, workload):
+    """The automatic halo exchange: pull for the unit-disk graph in RCM order (its CTAs' halos
+    lie in a few long runs), push for the BA graph (scattered halos).  The other exchange,
+    forced, gives the same states bit for bit over 50 iterations."""
+    kind = workload.meta["kind"]
+    g = bench_graph(gn, workload)
+    assert g.exchange == {"udg": "pull", "ba": "push"}[kind]
+    other = dev_graph(gn, workload, reorder=REORDER[kind],
+                      gather=gn.GATHER_HALO_PUSH if kind == "udg" else gn.GATHER_HALO_PULL)
+    pk = dict(theta_bin=-1.0, check_every=10)
+    xa, ia = g.run(max_iters=50, tol=-1.0, params=gn.default_params(**pk))
+    xb, ib = other.run(max_iters=50, tol=-1.0, params=gn.default_params(**pk))
+    np.testing.assert_array_equal(to_np(xa), to_np(xb))
+    assert ia["objective"] == ib["objective"]
+
+
 def test_fullsize_sync_modes_bit_identical(gn, workload):
     """The complete run with neighbour synchronisation (the default on this path) and with a
     grid barrier after every iteration: the same states bit for bit, the same stop."""

@@ -212,16 +212,14 @@ def test_invalid_graphs_rejected(gn):
 
 
 @pytest.mark.parametrize("sync", ["grid", "neighbour"])
-@pytest.mark.parametrize("which", ["er20k", "udg20k_rcm"])
-def test_barrier_timeout_returns_status(gn, which, sync):
+@pytest.mark.parametrize("exchange", ["pull", "push"])
+def test_barrier_timeout_returns_status(gn, exchange, sync):
     """A wait that nothing satisfies hits its limit and returns GN_ERR_TIMEOUT; the context
-    stays usable.  Covers the grid barrier and both neighbour-flag waits (every warp polling a
-    short dependency list, warp 0 polling a long one)."""
-    if which == "er20k":
-        inst, reorder = inputs.er_graph(20000, 8.0, 1290), 0
-    else:
-        inst, reorder = inputs.unit_disk_graph(20000, 100000, 1293), 1
-    g = dev_graph(gn, inst, reorder=reorder, gather=GATHERS["halo"])
+    stays usable.  Covers the grid barrier and the neighbour-flag waits under both halo
+    exchanges."""
+    inst = inputs.er_graph(20000, 8.0, 1290)
+    g = dev_graph(gn, inst, gather=gn.GATHER_HALO_PULL if exchange == "pull" else gn.GATHER_HALO_PUSH)
+    assert g.exchange == exchange
     s = gn.SYNC_GRID if sync == "grid" else gn.SYNC_NEIGHBOUR
     p = gn.default_params(debug_unreachable_barrier=1, spin_limit=2000, sync=s)
     with pytest.raises(gn.GNError) as e:
@@ -231,28 +229,34 @@ def test_barrier_timeout_returns_status(gn, which, sync):
     assert info["status"] == "OK"
 
 
-@pytest.mark.parametrize("which", ["er2000", "udg20k_rcm", "ba20k"])
-def test_neighbour_sync_iterates_match_oracle(gn, which):
-    """Neighbour synchronisation between stop tests (check every 7 iterations, 20 iterations:
-    the flag waits run in 17 of them) against the oracle, and bit for bit against the grid
-    barrier.  The unit-disk graph in RCM order has short dependency lists (every warp polls),
-    the ER and BA graphs long ones (warp 0 polls)."""
+@pytest.mark.parametrize("which", ["er2000", "udg20k_rcm", "ba20k", "star5000"])
+def test_halo_exchanges_and_syncs_iterates_match_oracle(gn, which):
+    """The halo mode's two exchanges (pull: per-value gathers; push: inboxes fetched by bulk
+    copy) under both synchronisations, 20 iterations with a stop-test check every 7 (the
+    neighbour-flag waits run in 17 of them): every combination against the oracle, and all
+    four bit for bit equal (same arithmetic, same summation order)."""
     inst = {"er2000": lambda: inputs.workload_er_small(),
             "udg20k_rcm": lambda: inputs.unit_disk_graph(20000, 100000, 1294),
-            "ba20k": lambda: inputs.ba_graph(20000, 5, 1295)}[which]()
-    g = dev_graph(gn, inst, reorder=1 if which == "udg20k_rcm" else 0, gather=GATHERS["halo"])
-    assert g.gather == "halo"
+            "ba20k": lambda: inputs.ba_graph(20000, 5, 1295),
+            "star5000": lambda: inputs.small_graph("S", 5001, [(0, i) for i in range(1, 5001)],
+                                                   w=np.random.default_rng(4).uniform(1, 100, 5001))}[which]()
+    reorder = 1 if which == "udg20k_rcm" else 0
     pk = dict(theta_bin=-1.0, check_every=7)
-    xs = []
-    for s in (gn.SYNC_NEIGHBOUR, gn.SYNC_GRID):
-        x, info = g.run(max_iters=20, tol=-1.0, params=gn.default_params(sync=s, **pk))
-        assert info["iters"] == 20
-        xs.append((to_np(x).copy(), info))
     xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=20, tol=-1.0, p=oracle.params(**pk))
+    xs = []
+    for ex, gather in (("pull", gn.GATHER_HALO_PULL), ("push", gn.GATHER_HALO_PUSH)):
+        g = dev_graph(gn, inst, reorder=reorder, gather=gather)
+        assert g.gather == "halo" and g.exchange == ex
+        for s in (gn.SYNC_NEIGHBOUR, gn.SYNC_GRID):
+            x, info = g.run(max_iters=20, tol=-1.0, params=gn.default_params(sync=s, **pk))
+            assert info["iters"] == 20
+            xs.append((to_np(x).copy(), info))
+        g.close()
     assert_close_rel(xs[0][0], xo)
-    np.testing.assert_array_equal(xs[0][0], xs[1][0])
-    assert xs[0][1]["objective"] == xs[1][1]["objective"]
-    assert xs[0][1]["resid_l1"] == xs[1][1]["resid_l1"]
+    for x, info in xs[1:]:
+        np.testing.assert_array_equal(xs[0][0], x)
+        assert xs[0][1]["objective"] == info["objective"]
+        assert xs[0][1]["resid_l1"] == info["resid_l1"]
 
 
 @pytest.mark.parametrize("gather", ["halo", "global"])
