@@ -7,7 +7,7 @@
  *     x_i  <-  x_i / ( x_i + gamma * sum_{j in N(i)} (v_j / v_i) x_j ),   v = sqrt(w),
  *
  * on a sparse conflict graph until the state binarises into the indicator of a
- * maximal independent set (Thm. 3).  The library runs the iteration on the GPU in
+ * maximal independent set (Thm. 4).  The library runs the iteration on the GPU in
  * the weighted state y = v (.) x (App. B: y_i <- v_i y_i / ((I + gamma A) y)_i), in
  * FP32, with FP64 reductions.
  *
@@ -101,7 +101,7 @@ typedef struct {
   int status;           /* the gn_status returned */
   double resid_inf;     /* max_i |x_i^{k+1} - x_i^k| of the last step */
   double resid_l1;      /* sum_i |x_i^{k+1} - x_i^k| of the last step (FP64) */
-  double objective;     /* sum_i w_i x_i of the returned state (FP64), Thm. 4 */
+  double objective;     /* sum_i w_i x_i of the returned state (FP64), Thm. 3 */
   double energy;        /* E~(y) = 1/2 y^T (I + gamma A) y - v^T y (Sec. 3) of the state that
                            entered the last step, at that step's gamma (FP64) */
   long long safe_div_hits; /* steps where (B y)_i <= 1e-9 set x_i = 1/2 (appendix module) */
@@ -203,7 +203,7 @@ gn_status gn_extract_is(gn_graph* g, const float* x, uint8_t* mask, int32_t* mem
                         int32_t* count, double* weight);
 
 /*
- * gn_objective -- FP64 relaxed MWIS objective sum_i w_i x_i (Thm. 4) and the energy
+ * gn_objective -- FP64 relaxed MWIS objective sum_i w_i x_i (Thm. 3) and the energy
  * E~(y) = 1/2 y^T (I + gamma A) y - v^T y, y = v (.) x (Sec. 3), of a state x (NULL = the
  * state left by the last gn_run).  Either output may be NULL.
  */
@@ -211,7 +211,7 @@ gn_status gn_objective(gn_graph* g, const float* x, double gamma, double* obj, d
 
 /*
  * gn_backward -- reverse mode of the last recorded gn_run (params.record = 1: T fixed steps).
- * Derived from the step's Jacobian (App. F, Lemma 1 in its general form): with s = (I + gamma A) y
+ * Derived from the step's Jacobian (App. G, Lemma 2 in its general form): with s = (I + gamma A) y
  * and x' = y / s, the adjoint of y' = v (.) x' is
  *   gbar_y = v (.) gbar' / s - (I + gamma A)(v (.) gbar' (.) y / s^2),
  *   gbar_v += gbar' (.) x',

@@ -71,7 +71,7 @@ void gno_step(int n, const int32_t* rp, const int32_t* ci, const double* v, doub
   }
 }
 
-/* Thm. 4 (weighted mass): M_v(y) = sum v_i y_i = sum w_i x_i, the relaxed MWIS objective. */
+/* Thm. 3 (weighted mass): M_v(y) = sum v_i y_i = sum w_i x_i, the relaxed MWIS objective. */
 double gno_objective(int n, const double* w, const double* x) {
   double s = 0.0;
   for (int i = 0; i < n; ++i) s += w[i] * x[i];
@@ -223,7 +223,7 @@ int gno_extract_is(int n, const int32_t* rp, const int32_t* ci, const double* w,
   return GNO_OK;
 }
 
-/* Thm. 3, eq. (mis-stability): stab(M) = gamma * min_{i not in M} sum_{j in N(i) cap M}
+/* Thm. 4, eq. (mis-stability): stab(M) = gamma * min_{i not in M} sum_{j in N(i) cap M}
  * sqrt(w_j / w_i).  Returns +inf when every vertex is in M. */
 double gno_stability(int n, const int32_t* rp, const int32_t* ci, const double* w,
                      double gamma, const uint8_t* mask) {
@@ -242,7 +242,7 @@ double gno_stability(int n, const int32_t* rp, const int32_t* ci, const double* 
 
 /* Brute force over every independent set (n <= 31): the maximum weight W* and the
  * maximisers (weights within rel_tol * W* of W*), by include/exclude recursion in
- * vertex order.  Used to bound GN results on tiny graphs (Thm. 3, optimality). */
+ * vertex order.  Used to bound GN results on tiny graphs (Thm. 4, optimality). */
 typedef struct {
   int n;
   const uint32_t* nbr;

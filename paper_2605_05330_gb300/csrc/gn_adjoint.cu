@@ -3,7 +3,7 @@
 //
 // Forward, weighted state (App. B): y_{t+1} = v (.) y_t / d_t with d_t = (I + gamma_t A) y_t;
 // the run stores the state every S = ceil(sqrt(T)) steps (sqrt(T) checkpointing).
-// Reverse, derived from the step's Jacobian (App. F, Lemma 1 in its general form) and carried
+// Reverse, derived from the step's Jacobian (App. G, Lemma 2 in its general form) and carried
 // in log space: with u = log y the step is u'_i = log v_i + u_i - log d_i, so
 //   du'_i/du_i = 1 - x'_i = gamma s_i / d_i,   du'_i/du_j = -gamma y_j / d_i  (j in N(i)),
 //   du'_i/dv_i = 1 / v_i,

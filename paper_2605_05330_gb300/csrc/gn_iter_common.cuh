@@ -70,7 +70,7 @@ struct CheckAcc {
 };
 
 // The update of one row (global id rb + i), arithmetic only:
-//   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. WRGN in the weighted state, App. B)
+//   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. 3, WRGN, in the weighted state of Sec. 3 / App. B)
 //   d <= 1e-9: x' = 1/2 (the safe division of the appendix module)
 // Straight-line code (the safe division is a select), so a thread's rows can interleave.
 struct RowStep {

@@ -8,7 +8,7 @@
 //   update   d_i = y_i + gamma_k s_i = (B y)_i;  x_i' = y_i / d_i,  y_i' = v_i x_i'
 //            (d_i <= 1e-9: x_i' = 1/2, the safe division of the appendix module)
 //   check    every c iterations: max |x'-x| and the non-binary count (the stop test) plus
-//            FP64 sums of |x'-x|, w x' (Thm. 4) and y (d/2 - v) (= E~(y), Sec. 3)
+//            FP64 sums of |x'-x|, w x' (Thm. 3) and y (d/2 - v) (= E~(y), Sec. 3)
 //   barrier  a bounded grid barrier; at a check every CTA then reduces the same per-CTA
 //            partials in the same order, so all CTAs take the same stop decision.
 #include <algorithm>

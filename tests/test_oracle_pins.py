@@ -26,7 +26,7 @@ def _graph_from_golden(g):
 @pytest.mark.parametrize("fixture", ["wrgn_edge_step.txt", "wrgn_star_step.txt",
                                      "gn_fixed_point_7node.txt", "gn_p3_fixed_point.txt"])
 def test_step_worked_examples(fixture):
-    """Def. WRGN / App. A worked examples: one step equals the hand-computed values."""
+    """Def. 3 (WRGN) / App. A worked examples: one step equals the hand-computed values."""
     g = read_golden(fixture)
     inst = _graph_from_golden(g)
     x = np.array([float(t) for t in g["x"]])
@@ -101,7 +101,7 @@ def _k2(w0):
 
 
 def test_k2_interior_fixed_point_below_gamma_B():
-    """App. G: below gamma_B the K2 energy is convex and GN converges to the apex x_a
+    """App. H: below gamma_B the K2 energy is convex and GN converges to the apex x_a
     (printed closed form) from any start."""
     g = read_golden("k2_phase_thresholds.txt")
     w0 = float(g["w0"][0])
@@ -117,7 +117,7 @@ def test_k2_interior_fixed_point_below_gamma_B():
 
 @pytest.mark.parametrize("gam", [0.6, 1.0, 1.25, 1.5, 1.9])
 def test_k2_heavier_wins_between_gamma_B_and_gamma_D(gam):
-    """App. G: for gamma_B < gamma < gamma_D every start converges to the MIS {0} (heavier)."""
+    """App. H: for gamma_B < gamma < gamma_D every start converges to the MIS {0} (heavier)."""
     g = read_golden("k2_phase_thresholds.txt")
     w0 = float(g["w0"][0])
     assert float(g["gamma_B"][0]) < gam < float(g["gamma_D"][0])
@@ -129,7 +129,7 @@ def test_k2_heavier_wins_between_gamma_B_and_gamma_D(gam):
 
 
 def test_k2_separatrix_above_gamma_D():
-    """App. G: above gamma_D both MIS are stable; the apex x_a = 5/7 (gamma = 3) separates
+    """App. H: above gamma_D both MIS are stable; the apex x_a = 5/7 (gamma = 3) separates
     their basins on the simplex."""
     g = read_golden("k2_phase_thresholds.txt")
     w0 = float(g["w0"][0])
@@ -144,7 +144,7 @@ def test_k2_separatrix_above_gamma_D():
 
 
 def test_k2_equal_weights_larger_start_wins():
-    """App. G, unweighted K2 with gamma > 1: the larger initial value wins."""
+    """App. H, unweighted K2 with gamma > 1: the larger initial value wins."""
     inst = _k2(1.0)
     x, info = oracle.run(inst.row_ptr, inst.col_idx, inst.w, x0=[0.51, 0.49], max_iters=5000,
                          tol=0.0, p=oracle.params(gamma_mode=oracle.GAMMA_FIXED, gamma1=1.5))
@@ -219,7 +219,7 @@ def test_preconditioned_gradient_identity(seed):
 
 @pytest.mark.parametrize("seed", [41, 42])
 def test_replicator_identity(seed):
-    """Thm. 5 / App. H: with p = v y / M_v and f_i = v_i / ((I + gamma A)(p / v))_i, the next
+    """Thm. 5 / App. I: with p = v y / M_v and f_i = v_i / ((I + gamma A)(p / v))_i, the next
     weighted mass is the average fitness, M_v^{k+1} = sum_i p_i f_i, and p' = p f / fbar."""
     inst = inputs.er_graph(40, 5, seed)
     A = _dense(inst)
@@ -238,7 +238,7 @@ def test_replicator_identity(seed):
 
 @pytest.mark.parametrize("seed", [51, 52, 53, 54])
 def test_energy_descent_and_mass_growth_fixed_gamma(seed):
-    """Thm. 1 (strict energy descent) and Thm. 4 (weighted mass strictly increases from the
+    """Thm. 1 (strict energy descent) and Thm. 3 (weighted mass strictly increases from the
     first image of the map on), at fixed gamma."""
     inst = inputs.er_graph(120, 8, seed)
     T = 300
@@ -258,7 +258,7 @@ def test_energy_descent_and_mass_growth_fixed_gamma(seed):
 
 @pytest.mark.parametrize("seed", range(61, 69))
 def test_final_state_is_stable_mis(seed):
-    """Thm. 3 (binary regularisation) and Thm. 6 (tilted Motzkin-Straus): the pursuit run ends
+    """Thm. 4 (binary regularisation) and Thm. 6 (tilted Motzkin-Straus): the pursuit run ends
     on a binary MIS M with stab(M) > 1, E~ = -W(M)/2 and Q(r) = 1/W(M) at r = y / M_v."""
     inst = inputs.er_graph(150, 7, seed)
     p = oracle.params()
@@ -303,7 +303,7 @@ def test_brute_force_enumerator_matches_exhaustive_python(seed):
 
 @pytest.mark.parametrize("seed", range(81, 91))
 def test_gn_bounded_by_mwis_and_every_mwis_stable(seed):
-    """Thm. 3 (optimality): every MWIS is gamma-stable with stab >= gamma > 1; GN returns an
+    """Thm. 4 (optimality): every MWIS is gamma-stable with stab >= gamma > 1; GN returns an
     independent set of weight <= W* (n <= 20)."""
     inst = inputs.er_graph(18 + seed % 3, 3.5, seed)
     W, masks = oracle.mwis_enumerate(inst.row_ptr, inst.col_idx, inst.w)
@@ -360,7 +360,7 @@ def test_cross_normalisation_row_column_sums():
 
 
 def test_nonmember_decay_rate():
-    """Thm. 3 proof: near a binary fixed point M a non-member contracts by
+    """Thm. 4 proof (App. G): near a binary fixed point M a non-member contracts by
     1 / (gamma * sum_{j in N(i) cap M} sqrt(w_j / w_i)) per step (Jacobian diagonal)."""
     inst = inputs.er_graph(40, 4, 91)
     gam = 1.5
