@@ -124,30 +124,45 @@ gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes) {
 }
 
 // Reverse Cuthill-McKee over every component (BFS from a minimum-degree vertex, neighbours
-// visited in increasing degree), reversed.  perm[new] = old.
+// visited in increasing degree, ties in the order met), reversed.  perm[new] = old.  The
+// vertices are bucketed by degree (a stable counting sort) and each BFS frontier's few new
+// neighbours are placed by a stable insertion sort on their degrees.
 static void rcm_order(int n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
                       std::vector<int32_t>& perm) {
   perm.clear();
   perm.reserve(n);
+  std::vector<int32_t> deg(n);
+  int dmax = 0;
+  for (int i = 0; i < n; ++i) {
+    deg[i] = rp[i + 1] - rp[i];
+    dmax = std::max(dmax, deg[i]);
+  }
+  std::vector<int32_t> start(dmax + 2, 0), byDeg(n);
+  for (int i = 0; i < n; ++i) ++start[deg[i] + 1];
+  for (int d = 0; d <= dmax; ++d) start[d + 1] += start[d];
+  for (int i = 0; i < n; ++i) byDeg[start[deg[i]]++] = i;
   std::vector<char> seen(n, 0);
-  std::vector<int32_t> byDeg(n);
-  std::iota(byDeg.begin(), byDeg.end(), 0);
-  std::stable_sort(byDeg.begin(), byDeg.end(),
-                   [&](int a, int b) { return rp[a + 1] - rp[a] < rp[b + 1] - rp[b]; });
-  std::vector<int32_t> nb;
   for (int s : byDeg) {
     if (seen[s]) continue;
     size_t head = perm.size();
     perm.push_back(s);
     seen[s] = 1;
     while (head < perm.size()) {
-      int u = perm[head++];
-      nb.clear();
-      for (int k = rp[u]; k < rp[u + 1]; ++k)
-        if (!seen[ci[k]]) { seen[ci[k]] = 1; nb.push_back(ci[k]); }
-      std::stable_sort(nb.begin(), nb.end(),
-                       [&](int a, int b) { return rp[a + 1] - rp[a] < rp[b + 1] - rp[b]; });
-      perm.insert(perm.end(), nb.begin(), nb.end());
+      const int u = perm[head++];
+      const size_t first = perm.size();
+      for (int k = rp[u]; k < rp[u + 1]; ++k) {
+        const int v = ci[k];
+        if (seen[v]) continue;
+        seen[v] = 1;
+        // insert v after every already-placed neighbour of u with degree <= deg[v]
+        size_t pos = perm.size();
+        perm.push_back(v);
+        while (pos > first && deg[perm[pos - 1]] > deg[v]) {
+          perm[pos] = perm[pos - 1];
+          --pos;
+        }
+        perm[pos] = v;
+      }
     }
   }
   std::reverse(perm.begin(), perm.end());
@@ -358,14 +373,17 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
     std::vector<int32_t> iperm(n), rp2(n + 1), ci2((size_t)std::max<int64_t>(g->nnz, 1));
     for (int r = 0; r < n; ++r) iperm[perm[r]] = r;
     rp2[0] = 0;
-    for (int r = 0; r < n; ++r) {
-      const int o = perm[r];
-      int32_t* dst = ci2.data() + rp2[r];
-      const int d = rp[o + 1] - rp[o];
-      for (int k = 0; k < d; ++k) dst[k] = iperm[ci_src[rp[o] + k]];
-      std::sort(dst, dst + d);
-      rp2[r + 1] = rp2[r] + d;
-    }
+    for (int r = 0; r < n; ++r) rp2[r + 1] = rp2[r] + (rp[perm[r] + 1] - rp[perm[r]]);
+    // rows are independent: renumber and sort each on the host threads
+    parallel_for(n, 4096, [&](int lo, int hi, int) {
+      for (int r = lo; r < hi; ++r) {
+        const int o = perm[r];
+        int32_t* dst = ci2.data() + rp2[r];
+        const int d = rp[o + 1] - rp[o];
+        for (int k = 0; k < d; ++k) dst[k] = iperm[ci_src[rp[o] + k]];
+        std::sort(dst, dst + d);
+      }
+    });
     float* d_w2 = nullptr;
     GN_CUDA(cudaMalloc(&g->d_perm, sizeof(int32_t) * n));
     GN_CUDA(cudaMalloc(&g->d_iperm, sizeof(int32_t) * n));

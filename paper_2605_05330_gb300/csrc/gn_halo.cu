@@ -433,7 +433,8 @@ static constexpr double kPullDensity = 4.0;
 // Builds the blocks for the partition `part`, for the exchange `want` (GN_GATHER_HALO: by
 // the halo density; GN_GATHER_HALO_PULL / _PUSH: that one).  Sets *fits = false (and builds
 // nothing on the device) when a CTA's working set does not fit shared memory or 16-bit local
-// ids; with the automatic choice the other exchange is tried before giving up.
+// ids; with the automatic choice the other exchange is tried before giving up.  The per-CTA
+// work runs on the host threads (parallel_for); every CTA's output is its own.
 static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
                                    const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
                                    const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits);
@@ -444,30 +445,47 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   const int nb = (int)part.size() - 1;
   const int n = g->n;
 
-  // halos (sorted external neighbour ids) and inbox offsets
+  // halos: each CTA's distinct external neighbours in increasing id order, from a bitmap of
+  // the vertex range (a mark per entry, then a scan of the marked words), and the number of
+  // 32-byte sectors of the state vector they touch
   std::vector<std::vector<int32_t>> ext(nb);
-  std::vector<int64_t> inbox_off(nb + 1, 0);
-  {
-    std::vector<int32_t> stamp(std::max(n, 1), -1);
-    for (int b = 0; b < nb; ++b) {
+  std::vector<int64_t> sectors_of(nb, 0);
+  parallel_for(nb, 1, [&](int lo, int hi, int) {
+    std::vector<uint64_t> bits((size_t)n / 64 + 1, 0);
+    for (int b = lo; b < hi; ++b) {
       const int rb = part[b], re = part[b + 1];
+      int wlo = INT32_MAX, whi = -1;
       for (int64_t e = rp[rb]; e < rp[re]; ++e) {
         const int j = ci[e];
-        if ((j < rb || j >= re) && stamp[j] != b) {
-          stamp[j] = b;
-          ext[b].push_back(j);
+        if (j >= rb && j < re) continue;
+        bits[j >> 6] |= 1ull << (j & 63);
+        wlo = std::min(wlo, j >> 6);
+        whi = std::max(whi, j >> 6);
+      }
+      std::vector<int32_t>& xb = ext[b];
+      int64_t sec = 0, last = -1;
+      for (int wd = wlo; wd <= whi; ++wd) {
+        uint64_t m = bits[wd];
+        bits[wd] = 0;
+        while (m) {
+          const int j = wd * 64 + __builtin_ctzll(m);
+          m &= m - 1;
+          xb.push_back(j);
+          sec += (j / 8 != last);
+          last = j / 8;
         }
       }
-      std::sort(ext[b].begin(), ext[b].end());
-      inbox_off[b + 1] = inbox_off[b] + (int64_t)((ext[b].size() + 3) & ~(size_t)3);
+      sectors_of[b] = sec;
     }
-  }
-  // the exchange: forced, or by the density of the halos in memory
+  });
+  std::vector<int64_t> inbox_off(nb + 1, 0);
   int64_t vals = 0, sectors = 0;
   for (int b = 0; b < nb; ++b) {
+    inbox_off[b + 1] = inbox_off[b] + (int64_t)((ext[b].size() + 3) & ~(size_t)3);
     vals += (int64_t)ext[b].size();
-    for (size_t t = 0; t < ext[b].size(); ++t) sectors += (t == 0 || ext[b][t] / 8 != ext[b][t - 1] / 8);
+    sectors += sectors_of[b];
   }
+  // the exchange: forced, or by the density of the halos in memory
   bool push = want == GN_GATHER_HALO_PUSH ||
               (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
   if (push && inbox_off[nb] > (int64_t)INT32_MAX) {  // inbox slots do not fit 32 bits
@@ -484,8 +502,8 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
 
 // The blocks for one exchange (see build_halo).
 static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
-                            const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
-                            const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits) {
+                                   const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                                   const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits) {
   *fits = false;
   const int nb = (int)part.size() - 1;
   const int n = g->n;
@@ -493,142 +511,155 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
   const int R = (max_rows + 3) & ~3;
   auto owner = [&](int j) { return (int)(std::upper_bound(part.begin(), part.end(), j) - part.begin()) - 1; };
-  // send lists: for each owner, the (inbox slot, own row) pairs in slot order.  Walking the
-  // consumers in order and each consumer's halo in order visits every owner's slots in
-  // increasing order, so each owner's list is sorted as built.
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
-  for (int c = 0; push && c < nb; ++c)
-    for (size_t t = 0; t < ext[c].size(); ++t) {
-      const int j = ext[c][t];
-      const int o = owner(j);
-      sends[o].push_back({(int32_t)(inbox_off[c] + (int64_t)t), j - part[o]});
-    }
 
+  // send lists: for each owner o, the (inbox slot, own row) pairs in slot order.  The slots of
+  // consumer c come before those of c + 1, and within c's halo (sorted by id) the vertices of
+  // o are one run, found by binary search.
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
+  if (push) {
+    parallel_for(nb, 1, [&](int lo, int hi, int) {
+      for (int o = lo; o < hi; ++o) {
+        for (int c = 0; c < nb; ++c) {
+          const std::vector<int32_t>& xc = ext[c];
+          const size_t t0 = std::lower_bound(xc.begin(), xc.end(), part[o]) - xc.begin();
+          const size_t t1 = std::lower_bound(xc.begin() + t0, xc.end(), part[o + 1]) - xc.begin();
+          for (size_t t = t0; t < t1; ++t)
+            sends[o].push_back({(int32_t)(inbox_off[c] + (int64_t)t), xc[t] - part[o]});
+        }
+      }
+    });
+  }
+
+  // pass 1, per CTA: rows into interior / boundary / heavy, slices, chunks, send pieces and
+  // the block layout
   std::vector<std::vector<unsigned char>> blocks(nb);
-  std::vector<int32_t> extpos(std::max(n, 1), 0);
+  parallel_for(nb, 1, [&](int lo, int hi, int) {
+    for (int b = lo; b < hi; ++b) {
+      const int rb = part[b], re = part[b + 1], nr = re - rb;
+      const std::vector<int32_t>& xb = ext[b];
+      // the CTAs owning the halo (xb is sorted, the partition is contiguous)
+      std::vector<int32_t> dep;
+      for (int j : xb) {
+        const int o = owner(j);
+        if (dep.empty() || dep.back() != o) dep.push_back(o);
+      }
+      std::vector<int> light_int, light_bnd, heavy;
+      for (int r = 0; r < nr; ++r) {
+        const int64_t a = rp[rb + r], c = rp[rb + r + 1];
+        if (c - a > kHeavyHalo) {
+          heavy.push_back(r);
+          continue;
+        }
+        bool bnd = false;
+        for (int64_t e = a; e < c && !bnd; ++e) bnd = (ci[e] < rb || ci[e] >= re);
+        (bnd ? light_bnd : light_int).push_back(r);
+      }
+      auto by_deg = [&](int x, int y) {
+        const int dx = rp[rb + x + 1] - rp[rb + x], dy = rp[rb + y + 1] - rp[rb + y];
+        return dx != dy ? dx > dy : x < y;
+      };
+      std::sort(light_int.begin(), light_int.end(), by_deg);
+      std::sort(light_bnd.begin(), light_bnd.end(), by_deg);
+      // interior-only slices first; the rest (the interior tail + boundary rows) after
+      const int ns_int = (int)light_int.size() / 32;
+      std::vector<int> order(light_int.begin(), light_int.end());
+      order.insert(order.end(), light_bnd.begin(), light_bnd.end());
+      const int ns = ((int)order.size() + 31) / 32;
+      HaloHeader H;
+      memset(&H, 0, sizeof H);
+      H.ns_int = ns_int;
+      H.ns = ns;
+      H.nheavy = (int)heavy.size();
+      H.lx = (int)xb.size();
+      H.ndep = (int)dep.size();
+      H.inbox_off = (int)inbox_off[b];
+      std::vector<int2> meta(ns);
+      std::vector<short> srow((size_t)ns * 32, (short)-1);
+      int sell_len = 0;
+      for (int s = 0; s < ns; ++s) {
+        int wmax = 0;
+        for (int l = 0; l < 32; ++l) {
+          const size_t q = (size_t)s * 32 + l;
+          if (q < order.size()) {
+            const int r = order[q];
+            srow[q] = (short)r;
+            wmax = std::max(wmax, (int)(rp[rb + r + 1] - rp[rb + r]));
+          }
+        }
+        wmax = (wmax + 3) & ~3;
+        meta[s] = make_int2(sell_len, wmax);
+        sell_len += wmax * 32;
+      }
+      // heavy rows: (row, first chunk, chunks); chunks: (entry offset into hl, count)
+      int heavy_len = 0;
+      std::vector<int> hmeta, hchunk;
+      for (int r : heavy) {
+        const int d = rp[rb + r + 1] - rp[rb + r];
+        hmeta.push_back(r);
+        hmeta.push_back((int)hchunk.size() / 2);
+        hmeta.push_back((d + kHeavyChunk - 1) / kHeavyChunk);
+        for (int a = 0; a < d; a += kHeavyChunk) {
+          hchunk.push_back(heavy_len + a);
+          hchunk.push_back(std::min(kHeavyChunk, d - a));
+        }
+        heavy_len += d;
+      }
+      H.sell_len = sell_len;
+      H.heavy_len = heavy_len;
+      H.nchunk = (int)hchunk.size() / 2;
+      // send pieces: runs of consecutive inbox slots, at most kSendPiece long
+      const std::vector<std::pair<int32_t, int32_t>>& sd = sends[b];
+      std::vector<int4> pieces;
+      std::vector<uint16_t> src(sd.size());
+      for (size_t e = 0; e < sd.size(); ++e) {
+        src[e] = (uint16_t)sd[e].second;
+        if (pieces.empty() || pieces.back().y == kSendPiece || sd[e].first != pieces.back().x + pieces.back().y)
+          pieces.push_back(make_int4(sd[e].first, 0, (int)e, 0));
+        ++pieces.back().y;
+      }
+      H.npiece = (int)pieces.size();
+      size_t off = align16(sizeof(HaloHeader));
+      H.off_meta = (int)off;
+      off = align16(off + sizeof(int2) * ns);
+      H.off_srow = (int)off;
+      off = align16(off + sizeof(short) * 32 * (size_t)ns);
+      H.off_sell = (int)off;
+      off = align16(off + 2 * (size_t)sell_len);
+      H.off_hmeta = (int)off;
+      off = align16(off + 4 * hmeta.size());
+      H.off_hl = (int)off;
+      off = align16(off + 2 * (size_t)heavy_len);
+      H.off_dep = (int)off;
+      off = align16(off + 4 * dep.size());
+      H.off_hchunk = (int)off;
+      off = align16(off + 4 * hchunk.size());
+      H.off_hpart = (int)off;
+      off = align16(off + 4 * (size_t)H.nchunk);
+      H.off_piece = (int)off;
+      off = align16(off + sizeof(int4) * pieces.size());
+      H.off_src = (int)off;
+      off = align16(off + 2 * src.size());
+      H.off_x = (int)off;
+      if (!push) off = align16(off + 4 * xb.size());
+      H.bytes = (int)off;
+      std::vector<unsigned char>& B = blocks[b];
+      B.assign(off, 0);
+      memcpy(B.data(), &H, sizeof H);
+      if (ns) memcpy(B.data() + H.off_meta, meta.data(), sizeof(int2) * ns);
+      if (ns) memcpy(B.data() + H.off_srow, srow.data(), sizeof(short) * 32 * (size_t)ns);
+      if (!hmeta.empty()) memcpy(B.data() + H.off_hmeta, hmeta.data(), 4 * hmeta.size());
+      if (!dep.empty()) memcpy(B.data() + H.off_dep, dep.data(), 4 * dep.size());
+      if (!hchunk.empty()) memcpy(B.data() + H.off_hchunk, hchunk.data(), 4 * hchunk.size());
+      if (!pieces.empty()) memcpy(B.data() + H.off_piece, pieces.data(), sizeof(int4) * pieces.size());
+      if (!src.empty()) memcpy(B.data() + H.off_src, src.data(), 2 * src.size());
+      if (!push && !xb.empty()) memcpy(B.data() + H.off_x, xb.data(), 4 * xb.size());
+    }
+  });
   int lx_max = 0;
   size_t blk_max = 0;
   for (int b = 0; b < nb; ++b) {
-    const int rb = part[b], re = part[b + 1], nr = re - rb;
-    const std::vector<int32_t>& xb = ext[b];
-    lx_max = std::max(lx_max, (int)xb.size());
-    // the CTAs owning the halo (xb is sorted, the partition is contiguous)
-    std::vector<int32_t> dep;
-    for (int j : xb) {
-      const int o = owner(j);
-      if (dep.empty() || dep.back() != o) dep.push_back(o);
-    }
-    std::vector<int> light_int, light_bnd, heavy;
-    for (int r = 0; r < nr; ++r) {
-      const int64_t a = rp[rb + r], c = rp[rb + r + 1];
-      if (c - a > kHeavyHalo) {
-        heavy.push_back(r);
-        continue;
-      }
-      bool bnd = false;
-      for (int64_t e = a; e < c && !bnd; ++e) bnd = (ci[e] < rb || ci[e] >= re);
-      (bnd ? light_bnd : light_int).push_back(r);
-    }
-    auto by_deg = [&](int x, int y) {
-      const int dx = rp[rb + x + 1] - rp[rb + x], dy = rp[rb + y + 1] - rp[rb + y];
-      return dx != dy ? dx > dy : x < y;
-    };
-    std::sort(light_int.begin(), light_int.end(), by_deg);
-    std::sort(light_bnd.begin(), light_bnd.end(), by_deg);
-    // interior-only slices first; the rest (the interior tail + boundary rows) after
-    const int ns_int = (int)light_int.size() / 32;
-    std::vector<int> order(light_int.begin(), light_int.end());
-    order.insert(order.end(), light_bnd.begin(), light_bnd.end());
-    const int ns = ((int)order.size() + 31) / 32;
-    HaloHeader H;
-    memset(&H, 0, sizeof H);
-    H.ns_int = ns_int;
-    H.ns = ns;
-    H.nheavy = (int)heavy.size();
-    H.lx = (int)xb.size();
-    H.ndep = (int)dep.size();
-    H.inbox_off = (int)inbox_off[b];
-    std::vector<int2> meta(ns);
-    std::vector<short> srow((size_t)ns * 32, (short)-1);
-    int sell_len = 0;
-    for (int s = 0; s < ns; ++s) {
-      int wmax = 0;
-      for (int l = 0; l < 32; ++l) {
-        const size_t q = (size_t)s * 32 + l;
-        if (q < order.size()) {
-          const int r = order[q];
-          srow[q] = (short)r;
-          wmax = std::max(wmax, (int)(rp[rb + r + 1] - rp[rb + r]));
-        }
-      }
-      wmax = (wmax + 3) & ~3;
-      meta[s] = make_int2(sell_len, wmax);
-      sell_len += wmax * 32;
-    }
-    // heavy rows: (row, first chunk, chunks); chunks: (entry offset into hl, count)
-    int heavy_len = 0;
-    std::vector<int> hmeta, hchunk;
-    for (int r : heavy) {
-      const int d = rp[rb + r + 1] - rp[rb + r];
-      hmeta.push_back(r);
-      hmeta.push_back((int)hchunk.size() / 2);
-      hmeta.push_back((d + kHeavyChunk - 1) / kHeavyChunk);
-      for (int a = 0; a < d; a += kHeavyChunk) {
-        hchunk.push_back(heavy_len + a);
-        hchunk.push_back(std::min(kHeavyChunk, d - a));
-      }
-      heavy_len += d;
-    }
-    H.sell_len = sell_len;
-    H.heavy_len = heavy_len;
-    H.nchunk = (int)hchunk.size() / 2;
-    // send pieces: runs of consecutive inbox slots, at most kSendPiece long
-    const std::vector<std::pair<int32_t, int32_t>>& sd = sends[b];
-    std::vector<int4> pieces;
-    std::vector<uint16_t> src(sd.size());
-    for (size_t e = 0; e < sd.size(); ++e) {
-      src[e] = (uint16_t)sd[e].second;
-      if (pieces.empty() || pieces.back().y == kSendPiece || sd[e].first != pieces.back().x + pieces.back().y)
-        pieces.push_back(make_int4(sd[e].first, 0, (int)e, 0));
-      ++pieces.back().y;
-    }
-    H.npiece = (int)pieces.size();
-    size_t off = align16(sizeof(HaloHeader));
-    H.off_meta = (int)off;
-    off = align16(off + sizeof(int2) * ns);
-    H.off_srow = (int)off;
-    off = align16(off + sizeof(short) * 32 * (size_t)ns);
-    H.off_sell = (int)off;
-    off = align16(off + 2 * (size_t)sell_len);
-    H.off_hmeta = (int)off;
-    off = align16(off + 4 * hmeta.size());
-    H.off_hl = (int)off;
-    off = align16(off + 2 * (size_t)heavy_len);
-    H.off_dep = (int)off;
-    off = align16(off + 4 * dep.size());
-    H.off_hchunk = (int)off;
-    off = align16(off + 4 * hchunk.size());
-    H.off_hpart = (int)off;
-    off = align16(off + 4 * (size_t)H.nchunk);
-    H.off_piece = (int)off;
-    off = align16(off + sizeof(int4) * pieces.size());
-    H.off_src = (int)off;
-    off = align16(off + 2 * src.size());
-    H.off_x = (int)off;
-    if (!push) off = align16(off + 4 * xb.size());
-    H.bytes = (int)off;
-    blk_max = std::max(blk_max, off);
-    std::vector<unsigned char>& B = blocks[b];
-    B.assign(off, 0);
-    memcpy(B.data(), &H, sizeof H);
-    if (ns) memcpy(B.data() + H.off_meta, meta.data(), sizeof(int2) * ns);
-    if (ns) memcpy(B.data() + H.off_srow, srow.data(), sizeof(short) * 32 * (size_t)ns);
-    if (!hmeta.empty()) memcpy(B.data() + H.off_hmeta, hmeta.data(), 4 * hmeta.size());
-    if (!dep.empty()) memcpy(B.data() + H.off_dep, dep.data(), 4 * dep.size());
-    if (!hchunk.empty()) memcpy(B.data() + H.off_hchunk, hchunk.data(), 4 * hchunk.size());
-    if (!pieces.empty()) memcpy(B.data() + H.off_piece, pieces.data(), sizeof(int4) * pieces.size());
-    if (!src.empty()) memcpy(B.data() + H.off_src, src.data(), 2 * src.size());
-    if (!push && !xb.empty()) memcpy(B.data() + H.off_x, xb.data(), 4 * xb.size());
+    lx_max = std::max(lx_max, (int)ext[b].size());
+    blk_max = std::max(blk_max, blocks[b].size());
   }
   const int Lp = (lx_max + 3) & ~3;
   const int zero_id = R + Lp;
@@ -636,61 +667,67 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   const size_t smem = 4 * floats + blk_max;
   if (zero_id > 65535 || smem > smem_limit || R > 32767) return GN_OK;  // does not fit
 
-  // encode the 16-bit local ids: own row r -> r, external halo t -> R + t, padding -> zero
-  for (int b = 0; b < nb; ++b) {
-    const int rb = part[b], re = part[b + 1];
-    std::vector<unsigned char>& B = blocks[b];
-    HaloHeader* H = reinterpret_cast<HaloHeader*>(B.data());
-    H->zero_id = zero_id;
-    for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = (int32_t)t;
-    auto lid = [&](int j) -> uint16_t {
-      return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
-    };
-    const int2* meta = reinterpret_cast<const int2*>(B.data() + H->off_meta);
-    const short* srow = reinterpret_cast<const short*>(B.data() + H->off_srow);
-    uint16_t* sell = reinterpret_cast<uint16_t*>(B.data() + H->off_sell);
-    // Within a slice every lane's row may list its entries in any order.  Column by column,
-    // give each lane the unused entry whose shared-memory bank (local id mod 32) is least
-    // taken in that column, so the 32 lanes' gathers spread over the banks.
+  // pass 2, per CTA: the 16-bit local ids (own row r -> r, external halo t -> R + t,
+  // padding -> the zero slot)
+  parallel_for(nb, 1, [&](int lo, int hi, int) {
+    std::vector<int32_t> extpos(std::max(n, 1), 0);
     std::vector<std::vector<uint16_t>> pending(32);
-    for (int s = 0; s < H->ns; ++s) {
-      for (int l = 0; l < 32; ++l) {
-        const int r = srow[s * 32 + l];
-        pending[l].clear();
-        if (r >= 0)
-          for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) pending[l].push_back(lid(ci[e]));
-      }
-      for (int k = 0; k < meta[s].y; ++k) {
-        int load[32] = {0};
+    for (int b = lo; b < hi; ++b) {
+      const int rb = part[b], re = part[b + 1];
+      std::vector<unsigned char>& B = blocks[b];
+      HaloHeader* H = reinterpret_cast<HaloHeader*>(B.data());
+      H->zero_id = zero_id;
+      for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = (int32_t)t;
+      auto lid = [&](int j) -> uint16_t {
+        return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
+      };
+      const int2* meta = reinterpret_cast<const int2*>(B.data() + H->off_meta);
+      const short* srow = reinterpret_cast<const short*>(B.data() + H->off_srow);
+      uint16_t* sell = reinterpret_cast<uint16_t*>(B.data() + H->off_sell);
+      // Within a slice every lane's row may list its entries in any order.  Column by column,
+      // give each lane the unused entry whose shared-memory bank (local id mod 32) is least
+      // taken in that column, so the 32 lanes' gathers spread over the banks.
+      for (int s = 0; s < H->ns; ++s) {
         for (int l = 0; l < 32; ++l) {
-          std::vector<uint16_t>& q = pending[l];
-          uint16_t pick = (uint16_t)zero_id;
-          if (!q.empty()) {
-            size_t best = 0;
-            for (size_t t = 1; t < q.size() && load[q[best] & 31]; ++t)
-              if (load[q[t] & 31] < load[q[best] & 31]) best = t;
-            pick = q[best];
-            q[best] = q.back();
-            q.pop_back();
-            ++load[pick & 31];
+          const int r = srow[s * 32 + l];
+          pending[l].clear();
+          if (r >= 0)
+            for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) pending[l].push_back(lid(ci[e]));
+        }
+        for (int k = 0; k < meta[s].y; ++k) {
+          int load[32] = {0};
+          for (int l = 0; l < 32; ++l) {
+            std::vector<uint16_t>& q = pending[l];
+            uint16_t pick = (uint16_t)zero_id;
+            if (!q.empty()) {
+              size_t best = 0;
+              for (size_t t = 1; t < q.size() && load[q[best] & 31]; ++t)
+                if (load[q[t] & 31] < load[q[best] & 31]) best = t;
+              pick = q[best];
+              q[best] = q.back();
+              q.pop_back();
+              ++load[pick & 31];
+            }
+            sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = pick;
           }
-          sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = pick;
         }
       }
+      const int* hm = reinterpret_cast<const int*>(B.data() + H->off_hmeta);
+      const int* hc = reinterpret_cast<const int*>(B.data() + H->off_hchunk);
+      uint16_t* hl = reinterpret_cast<uint16_t*>(B.data() + H->off_hl);
+      for (int h = 0; h < H->nheavy; ++h) {
+        const int r = hm[3 * h], o = hc[2 * hm[3 * h + 1]];  // the row's entries start at its first chunk
+        const int d = rp[rb + r + 1] - rp[rb + r];
+        for (int k = 0; k < d; ++k) hl[o + k] = lid(ci[rp[rb + r] + k]);
+      }
     }
-    const int* hm = reinterpret_cast<const int*>(B.data() + H->off_hmeta);
-    const int* hc = reinterpret_cast<const int*>(B.data() + H->off_hchunk);
-    uint16_t* hl = reinterpret_cast<uint16_t*>(B.data() + H->off_hl);
-    for (int h = 0; h < H->nheavy; ++h) {
-      const int r = hm[3 * h], o = hc[2 * hm[3 * h + 1]];  // the row's entries start at its first chunk
-      const int d = rp[rb + r + 1] - rp[rb + r];
-      for (int k = 0; k < d; ++k) hl[o + k] = lid(ci[rp[rb + r] + k]);
-    }
-  }
+  });
   std::vector<int64_t> hoff(nb + 1, 0);
   for (int b = 0; b < nb; ++b) hoff[b + 1] = hoff[b] + (int64_t)blocks[b].size();
   std::vector<unsigned char> blob((size_t)std::max<int64_t>(hoff[nb], 16));
-  for (int b = 0; b < nb; ++b) memcpy(blob.data() + hoff[b], blocks[b].data(), blocks[b].size());
+  parallel_for(nb, 8, [&](int lo, int hi, int) {
+    for (int b = lo; b < hi; ++b) memcpy(blob.data() + hoff[b], blocks[b].data(), blocks[b].size());
+  });
   GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
   GN_CUDA(cudaMalloc(&g->d_hblob, blob.size()));
   if (push) {

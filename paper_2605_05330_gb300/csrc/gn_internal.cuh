@@ -5,7 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "gn.h"
 
@@ -153,6 +156,31 @@ gn_status to_internal(gn_graph* g, const float* x_caller, const float** x_int);
 // implemented in gn_graph.cu
 gn_status upload_or_alias(gn_graph* g, const void* src, size_t bytes, const void** dev_ptr);
 gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes);
+
+// Host-side preparation work over [0, n) split into contiguous blocks, one per host thread
+// (at most the hardware's count, and one per `grain` items): body(lo, hi, thread).  The
+// blocks are fixed by n and the thread count only, and every caller writes disjoint outputs,
+// so results do not depend on scheduling.
+inline int host_threads() {
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h == 0 ? 1u : h, 64u));
+}
+template <class F>
+void parallel_for(int n, int grain, F&& body) {
+  const int nt = std::max(1, std::min(host_threads(), (n + std::max(grain, 1) - 1) / std::max(grain, 1)));
+  if (nt <= 1) {
+    if (n > 0) body(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(nt - 1);
+  for (int t = 1; t < nt; ++t) {
+    const int lo = (int)((int64_t)n * t / nt), hi = (int)((int64_t)n * (t + 1) / nt);
+    pool.emplace_back([&body, lo, hi, t] { body(lo, hi, t); });
+  }
+  body(0, (int)((int64_t)n / nt), 0);
+  for (std::thread& th : pool) th.join();
+}
 
 }  // namespace gn
 
