@@ -24,7 +24,10 @@ namespace gn {
 static constexpr int kF = 4;      // input features
 static constexpr int kH = 64;     // hidden width
 static constexpr int kL = 3;      // layers
-static constexpr int kRows = 32;  // rows per CTA in the dense kernels
+static constexpr int kRows = 32;  // rows per tile in the dense kernels
+static constexpr int kHeadRows = 128;  // rows (threads) per CTA of the head
+static constexpr int kDenseThreads = 128;            // threads of the forward dense kernel
+static constexpr int kDenseRows = 8 * kDenseThreads / 8;  // its rows per tile: 8 per thread, 8 threads per row group
 
 __host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kF : kH; }
 // parameter layout (FP32): per layer Ws [kH x din], Wn [kH x din], b [kH]; then wo [kH], bo [1]
@@ -51,19 +54,62 @@ __global__ void k_features(int n, const int32_t* __restrict__ rp, const int32_t*
   X[(size_t)i * kF + 3] = mx;
 }
 
-// M_i = mean_{j in N(i)} H_j (0 for an isolated vertex); a warp per vertex, lanes over features
+// M_i = mean_{j in N(i)} H_j (0 for an isolated vertex), each feature summed over the
+// neighbours in CSR order.  D = kF (4 features): a thread per vertex, one 16-byte load per
+// neighbour.  D = kH: a warp per vertex, lane l owning features l and l + 32; the lanes read 32
+// neighbour ids at once and broadcast them, and four neighbours' rows are loaded before they
+// are added (in order).
 template <int D>
 __global__ void k_aggregate(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                             const float* __restrict__ H, float* __restrict__ M) {
+  static_assert(D == kF || D == kH, "aggregation widths");
+  if (D == kF) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int a = rp[i], b = rp[i + 1];
+    const float inv = b > a ? 1.0f / (float)(b - a) : 0.0f;
+    float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int e = a; e < b; ++e) {
+      const float4 h = reinterpret_cast<const float4*>(H)[ci[e]];
+      s.x += h.x;
+      s.y += h.y;
+      s.z += h.z;
+      s.w += h.w;
+    }
+    reinterpret_cast<float4*>(M)[i] = make_float4(s.x * inv, s.y * inv, s.z * inv, s.w * inv);
+    return;
+  }
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
   const int a = rp[i], b = rp[i + 1];
   const float inv = b > a ? 1.0f / (float)(b - a) : 0.0f;
-  for (int f = lane; f < D; f += 32) {
-    float s = 0.0f;
-    for (int e = a; e < b; ++e) s += H[(size_t)ci[e] * D + f];
-    M[(size_t)i * D + f] = s * inv;
+  float s0 = 0.0f, s1 = 0.0f;
+  for (int base = a; base < b; base += 32) {
+    const int cnt = min(32, b - base);
+    const int mine = lane < cnt ? ci[base + lane] : 0;
+    int t = 0;
+    for (; t + 4 <= cnt; t += 4) {
+      float h0[4], h1[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = __shfl_sync(0xffffffffu, mine, t + u);
+        h0[u] = H[(size_t)j * D + lane];
+        h1[u] = H[(size_t)j * D + lane + 32];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s0 += h0[u];
+        s1 += h1[u];
+      }
+    }
+    for (; t < cnt; ++t) {
+      const int j = __shfl_sync(0xffffffffu, mine, t);
+      s0 += H[(size_t)j * D + lane];
+      s1 += H[(size_t)j * D + lane + 32];
+    }
   }
+  M[(size_t)i * D + lane] = s0 * inv;
+  M[(size_t)i * D + lane + 32] = s1 * inv;
 }
 
 // the transpose: dH_j += sum_{i in N(j)} dM_i / deg_i (A symmetric)
@@ -83,44 +129,76 @@ __global__ void k_aggregate_t(int n, const int32_t* __restrict__ rp, const int32
   }
 }
 
-// Z = H Ws^T + M Wn^T + b, Hout = relu(Z); kRows rows per CTA, 256 threads, 8 outputs each
+// Z = H Ws^T + M Wn^T + b, Hout = relu(Z).  The CTA stages the layer's weights once and walks
+// tiles of kDenseRows rows (grid-stride) staged in shared memory (dynamic, [rows][2 DIN + 1]).
+// 128 threads; thread (c, g) computes rows 8g..8g+7 of the tile at outputs c, c + 8, ..., c + 56,
+// so each weight and each input read from shared memory feeds eight FMAs (the bank of a read
+// is c + 8q + k or 8g + i + k mod 32: no conflicts), and consecutive threads store consecutive
+// outputs.  Every output is the same FMA chain over k as a plain dot product.  Z is kept only
+// for training (nullptr: inference).
 template <int DIN>
-__global__ void __launch_bounds__(256) k_dense_fwd(int n, const float* __restrict__ H, const float* __restrict__ M,
-                                                   const __nv_bfloat16* __restrict__ Wb, float* __restrict__ Z,
-                                                   float* __restrict__ Hout) {
+__global__ void __launch_bounds__(kDenseThreads) k_dense_fwd(int n, const float* __restrict__ H,
+                                                             const float* __restrict__ M,
+                                                             const __nv_bfloat16* __restrict__ Wb,
+                                                             float* __restrict__ Z, float* __restrict__ Hout) {
   __shared__ float sW[2][kH][DIN + 1];
-  __shared__ float sX[kRows][2 * DIN + 1];
   __shared__ float sb[kH];
-  const int r0 = blockIdx.x * kRows;
+  extern __shared__ float sXd[];
+  float(*sX)[2 * DIN + 1] = reinterpret_cast<float(*)[2 * DIN + 1]>(sXd);
   for (int t = threadIdx.x; t < 2 * kH * DIN; t += blockDim.x) {
     const int m = t / (kH * DIN), rem = t % (kH * DIN);
     sW[m][rem / DIN][rem % DIN] = __bfloat162float(Wb[t]);
   }
   for (int t = threadIdx.x; t < kH; t += blockDim.x) sb[t] = __bfloat162float(Wb[2 * kH * DIN + t]);
-  for (int t = threadIdx.x; t < kRows * DIN; t += blockDim.x) {
-    const int r = t / DIN, k = t % DIN;
-    const bool in = r0 + r < n;
-    sX[r][k] = in ? H[(size_t)(r0 + r) * DIN + k] : 0.0f;
-    sX[r][DIN + k] = in ? M[(size_t)(r0 + r) * DIN + k] : 0.0f;
-  }
-  __syncthreads();
-  const int row = threadIdx.x >> 3, og = (threadIdx.x & 7) * 8;
-  float acc[8];
+  const int c = threadIdx.x & 7, g = threadIdx.x >> 3;
+  const int ntiles = (n + kDenseRows - 1) / kDenseRows;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int r0 = tile * kDenseRows;
+    __syncthreads();  // the weights (first tile) / the previous tile's reads of sX
+    for (int t = threadIdx.x; t < kDenseRows * DIN; t += blockDim.x) {
+      const int r = t / DIN, k = t % DIN;
+      const bool in = r0 + r < n;
+      sX[r][k] = in ? H[(size_t)(r0 + r) * DIN + k] : 0.0f;
+      sX[r][DIN + k] = in ? M[(size_t)(r0 + r) * DIN + k] : 0.0f;
+    }
+    __syncthreads();
+    float acc[8][8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) acc[q] = sb[og + q];
-  for (int k = 0; k < DIN; ++k) {
-    const float h = sX[row][k], m = sX[row][DIN + k];
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = fmaf(sW[0][og + q][k], h, fmaf(sW[1][og + q][k], m, acc[q]));
-  }
-  if (r0 + row < n) {
+      for (int q = 0; q < 8; ++q) acc[i][q] = sb[c + 8 * q];
+    for (int k = 0; k < DIN; ++k) {
+      float h[8], mm[8], ws[8], wn[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      Z[(size_t)(r0 + row) * kH + og + q] = acc[q];
-      Hout[(size_t)(r0 + row) * kH + og + q] = fmaxf(acc[q], 0.0f);
+      for (int i = 0; i < 8; ++i) {
+        h[i] = sX[8 * g + i][k];
+        mm[i] = sX[8 * g + i][DIN + k];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        ws[q] = sW[0][c + 8 * q][k];
+        wn[q] = sW[1][c + 8 * q][k];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[i][q] = fmaf(ws[q], h[i], fmaf(wn[q], mm[i], acc[i][q]));
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = r0 + 8 * g + i;
+      if (r < n) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (Z) Z[(size_t)r * kH + c + 8 * q] = acc[i][q];
+          Hout[(size_t)r * kH + c + 8 * q] = fmaxf(acc[i][q], 0.0f);
+        }
+      }
     }
   }
 }
+template <int DIN>
+constexpr size_t dense_fwd_smem() { return sizeof(float) * (size_t)kDenseRows * (2 * DIN + 1); }
 
 // dZ = dHout (.) [Z > 0]; dH = dZ Ws, dM = dZ Wn (per row); kRows rows per CTA
 template <int DIN>
@@ -207,19 +285,29 @@ __global__ void __launch_bounds__(256) k_dense_bwd_weight(int n, int rows_per_ct
 // head: q = wo . h + bo, p = sigmoid(q); BCE loss (stable form) and dq = (p - t) / n; x0 out.
 // With alpha < 1 the start blends the prediction with the cold start geometrically:
 // x0 = clamp((1/(deg+1))^(1-alpha) p^alpha, 1e-3, 1).
-__global__ void k_head(int n, const float* __restrict__ H, const __nv_bfloat16* __restrict__ wo_b,
-                       const float* __restrict__ target, const int32_t* __restrict__ perm_int_to_caller,
-                       float* __restrict__ x0_caller, float* __restrict__ dq, double* __restrict__ loss,
-                       const int32_t* __restrict__ rp, float alpha) {
+// (kHeadRows threads; the CTA's rows of H are staged in shared memory with coalesced loads)
+__global__ void __launch_bounds__(kHeadRows) k_head(int n, const float* __restrict__ H,
+                                                    const __nv_bfloat16* __restrict__ wo_b,
+                                                    const float* __restrict__ target,
+                                                    const int32_t* __restrict__ perm_int_to_caller,
+                                                    float* __restrict__ x0_caller, float* __restrict__ dq,
+                                                    double* __restrict__ loss, const int32_t* __restrict__ rp,
+                                                    float alpha) {
   __shared__ float swo[kH + 1];
-  __shared__ double sl[8];
+  __shared__ double sl[kHeadRows / 32];
+  __shared__ float sH[kHeadRows][kH + 1];
   for (int t = threadIdx.x; t <= kH; t += blockDim.x) swo[t] = __bfloat162float(wo_b[t]);
+  const int i0 = blockIdx.x * kHeadRows;
+  for (int t = threadIdx.x; t < kHeadRows * kH; t += blockDim.x) {
+    const int r = t / kH, k = t % kH;
+    sH[r][k] = i0 + r < n ? H[(size_t)(i0 + r) * kH + k] : 0.0f;
+  }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = i0 + threadIdx.x;
   double l = 0.0;
   if (i < n) {
     float q = swo[kH];
-    for (int k = 0; k < kH; ++k) q = fmaf(swo[k], H[(size_t)i * kH + k], q);
+    for (int k = 0; k < kH; ++k) q = fmaf(swo[k], sH[threadIdx.x][k], q);
     const float p = 1.0f / (1.0f + expf(-q));
     const int c = perm_int_to_caller ? perm_int_to_caller[i] : i;
     if (x0_caller) {
@@ -300,6 +388,7 @@ __global__ void k_gather_caller(int n, const float* __restrict__ src_caller, con
 
 struct gn_mpnn {
   int device = 0;
+  int num_sms = 1;
   cudaStream_t stream = nullptr;
   float* d_w = nullptr;             // FP32 masters
   __nv_bfloat16* d_wb = nullptr;    // bf16 copy used by the kernels
@@ -385,6 +474,11 @@ extern "C" gn_status gn_mpnn_create(gn_mpnn** out, const float* init_params_host
     ~Guard() { if (m) gn_mpnn_destroy(m); }
   } guard{m};
   GN_CUDA(cudaGetDevice(&m->device));
+  GN_CUDA(cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device));
+  GN_CUDA(cudaFuncSetAttribute((const void*)k_dense_fwd<kH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dense_fwd_smem<kH>()));
+  GN_CUDA(cudaFuncSetAttribute((const void*)k_dense_fwd<kF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dense_fwd_smem<kF>()));
   m->stream = (cudaStream_t)stream;
   const size_t nb = sizeof(float) * kNumParams;
   GN_CUDA(cudaMalloc(&m->d_w, nb));
@@ -438,15 +532,20 @@ static gn_status mpnn_forward_impl(gn_mpnn* m, const gn_graph* g, float* x0_out,
   const float* Hin = m->X;
   for (int l = 0; l < kL; ++l) {
     const __nv_bfloat16* Wb = m->d_wb + layer_off(l);
+    // the dense layers: a grid of a few CTAs per SM walking the row tiles
+    const int tiles = (n + kDenseRows - 1) / kDenseRows;
+    float* Z = target ? m->Zs[l] : nullptr;  // pre-activations only for the backward
     if (l == 0) {
-      k_aggregate<kF><<<blk((int64_t)n * 32, 256), 256, 0, s>>>(n, g->d_row_ptr, g->d_col_idx, Hin, m->Ms[l]);
+      k_aggregate<kF><<<blk(n, 256), 256, 0, s>>>(n, g->d_row_ptr, g->d_col_idx, Hin, m->Ms[l]);
       GN_LAUNCHED();
-      k_dense_fwd<kF><<<blk(n, kRows), 256, 0, s>>>(n, Hin, m->Ms[l], Wb, m->Zs[l], m->Hs[l]);
+      k_dense_fwd<kF><<<std::min(tiles, 8 * m->num_sms), kDenseThreads, dense_fwd_smem<kF>(), s>>>(
+          n, Hin, m->Ms[l], Wb, Z, m->Hs[l]);
       GN_LAUNCHED();
     } else {
       k_aggregate<kH><<<blk((int64_t)n * 32, 256), 256, 0, s>>>(n, g->d_row_ptr, g->d_col_idx, Hin, m->Ms[l]);
       GN_LAUNCHED();
-      k_dense_fwd<kH><<<blk(n, kRows), 256, 0, s>>>(n, Hin, m->Ms[l], Wb, m->Zs[l], m->Hs[l]);
+      k_dense_fwd<kH><<<std::min(tiles, 2 * m->num_sms), kDenseThreads, dense_fwd_smem<kH>(), s>>>(
+          n, Hin, m->Ms[l], Wb, Z, m->Hs[l]);
       GN_LAUNCHED();
     }
     Hin = m->Hs[l];
@@ -457,8 +556,8 @@ static gn_status mpnn_forward_impl(gn_mpnn* m, const gn_graph* g, float* x0_out,
   }
   GN_CUDA(cudaMemsetAsync(m->d_loss, 0, sizeof(double), s));
   // the head reads targets in caller order through the permutation
-  k_head<<<blk(n, 256), 256, 0, s>>>(n, m->Hs[kL - 1], m->d_wb + layer_off(kL), target, g->d_perm, x0_out, m->dq,
-                                     m->d_loss, g->d_row_ptr, alpha);
+  k_head<<<blk(n, kHeadRows), kHeadRows, 0, s>>>(n, m->Hs[kL - 1], m->d_wb + layer_off(kL), target, g->d_perm,
+                                                 x0_out, m->dq, m->d_loss, g->d_row_ptr, alpha);
   GN_LAUNCHED();
   GN_CUDA(cudaGetLastError());
   m->n = n;
