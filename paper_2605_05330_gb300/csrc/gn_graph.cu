@@ -4,6 +4,7 @@
 // locality, and partitions the rows across the persistent kernel's CTAs.
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -125,39 +126,41 @@ gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes) {
 
 // Reverse Cuthill-McKee over every component (BFS from a minimum-degree vertex, neighbours
 // visited in increasing degree, ties in the order met), reversed.  perm[new] = old.  The
-// vertices are bucketed by degree (a stable counting sort) and each BFS frontier's few new
-// neighbours are placed by a stable insertion sort on their degrees.
+// vertices are bucketed by degree (a stable counting sort); each BFS step places its new
+// neighbours by a stable insertion sort on degree.  key[v] holds the degree with the sign bit
+// set once v is placed, so each neighbour costs one random access (the traversal is bound by
+// those on graphs with random labels).
 static void rcm_order(int n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
                       std::vector<int32_t>& perm) {
   perm.clear();
   perm.reserve(n);
-  std::vector<int32_t> deg(n);
+  std::vector<int32_t> key(n);
   int dmax = 0;
   for (int i = 0; i < n; ++i) {
-    deg[i] = rp[i + 1] - rp[i];
-    dmax = std::max(dmax, deg[i]);
+    key[i] = rp[i + 1] - rp[i];
+    dmax = std::max(dmax, key[i]);
   }
   std::vector<int32_t> start(dmax + 2, 0), byDeg(n);
-  for (int i = 0; i < n; ++i) ++start[deg[i] + 1];
+  for (int i = 0; i < n; ++i) ++start[key[i] + 1];
   for (int d = 0; d <= dmax; ++d) start[d + 1] += start[d];
-  for (int i = 0; i < n; ++i) byDeg[start[deg[i]]++] = i;
-  std::vector<char> seen(n, 0);
+  for (int i = 0; i < n; ++i) byDeg[start[key[i]]++] = i;
+  constexpr int32_t kPlaced = INT32_MIN;
   for (int s : byDeg) {
-    if (seen[s]) continue;
+    if (key[s] < 0) continue;
     size_t head = perm.size();
     perm.push_back(s);
-    seen[s] = 1;
+    key[s] |= kPlaced;
     while (head < perm.size()) {
       const int u = perm[head++];
       const size_t first = perm.size();
       for (int k = rp[u]; k < rp[u + 1]; ++k) {
         const int v = ci[k];
-        if (seen[v]) continue;
-        seen[v] = 1;
-        // insert v after every already-placed neighbour of u with degree <= deg[v]
+        const int32_t kv = key[v];
+        if (kv < 0) continue;
+        key[v] = kv | kPlaced;
         size_t pos = perm.size();
         perm.push_back(v);
-        while (pos > first && deg[perm[pos - 1]] > deg[v]) {
+        while (pos > first && (key[perm[pos - 1]] & INT32_MAX) > kv) {
           perm[pos] = perm[pos - 1];
           --pos;
         }
