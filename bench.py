@@ -71,10 +71,31 @@ def dist_env():
 REORDER = {"udg": 1, "ba": 0}
 
 
-def make_workload(rank: int):
+def workload_seeds(rank: int):
+    """Seeds of the two graphs of rank `rank`: each replica gets its own workload."""
     from paper_2605_05330_gb300 import inputs
     base = inputs.SEED_BASE + 1000 * rank
-    return [inputs.workload_udg_1m(seed=base), inputs.workload_ba_1m(seed=base + 1)]
+    return base, base + 1
+
+
+def make_workload(rank: int):
+    from paper_2605_05330_gb300 import inputs
+    s_udg, s_ba = workload_seeds(rank)
+    return [inputs.workload_udg_1m(seed=s_udg), inputs.workload_ba_1m(seed=s_ba)]
+
+
+def combine_ranks(ms_step: float, units_step: float, device):
+    """Replicas: the slowest rank's step time (max) and the units all ranks processed (sum).
+    A single process returns its own numbers."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_step, units_step
+    t = torch.tensor([ms_step], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units_step], device=device, dtype=torch.float64)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def bytes_per_iter(inst) -> int:
@@ -505,14 +526,7 @@ def main():
 
     ms_step = statistics.mean(times)
     units_step = sum(inst.nnz * info["iters"] for inst, info, _, _ in records) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-        u = torch.tensor([units_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units_step = float(u.item())
+    ms_step, units_step = combine_ranks(ms_step, units_step, dev)
     value = units_step / (ms_step / 1000.0)
 
     # roofline of the dominant kernel (the persistent iteration kernel): algorithmic bytes per
@@ -580,16 +594,7 @@ def main():
             units, h2d, d2h = e2e_step()
             torch.cuda.synchronize()
             tt.append(time.perf_counter() - t0)
-        e2e_s = statistics.mean(tt)
-        e2e_units = units
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-            u = torch.tensor([float(units)], device=dev, dtype=torch.float64)
-            dist.all_reduce(u, op=dist.ReduceOp.SUM)
-            e2e_units = float(u.item())
+        e2e_s, e2e_units = combine_ranks(statistics.mean(tt), float(units), dev)
         e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": 1000 * e2e_s}
 

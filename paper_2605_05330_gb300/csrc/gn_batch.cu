@@ -57,7 +57,8 @@ struct BatchParams {
   int check_every;
   double theta;
   double tol;
-  int nmax;                 // largest instance (shared-memory layout)
+  int nmax;                 // largest instance (the state arrays of the shared-memory layout)
+  int ncsr;                 // largest CSR instance (its neighbour sums and row offsets)
   int idcap;                // local ids held in shared memory up to this many entries
 };
 
@@ -97,27 +98,30 @@ __device__ __forceinline__ dev::f2 block_sum_pair(dev::f2 v, float* shh, float* 
   return t;
 }
 
-__global__ void __launch_bounds__(kBatchMaxThreads) k_gn_batch(const BatchParams P) {
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_inst;
   __shared__ float s_rf[32];
   __shared__ unsigned s_ru[32];
   __shared__ float s_ph[32], s_pl[32];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int N = P.nmax;
+  // shared memory: [y_hi y_lo x v_hi v_lo (nmax each) | row and column sums as float pairs
+  // (assignment, k <= 128) | neighbour sums, row offsets (CSR, ncsr) | local ids (CSR)].
+  // Assignment instances form their neighbour sums inside the update, so a k = 96 instance
+  // (9216 vertices) fits.
+  const int N = P.nmax, NC = P.ncsr;
   float* s_yh = reinterpret_cast<float*>(smem);
   float* s_yl = s_yh + N;
   float* s_x = s_yl + N;
   float* s_vh = s_x + N;
   float* s_vl = s_vh + N;
-  float* s_sum = s_vl + N;
-  // assignment instances: row and column sums as float pairs (k <= sqrt(nmax) each)
-  float* s_rh = s_sum + N;
+  float* s_rh = s_vl + N;
   float* s_rl = s_rh + 128;
   float* s_ch = s_rl + 128;
   float* s_cl = s_ch + 128;
-  int* s_rp = reinterpret_cast<int*>(s_cl + 128);
-  uint16_t* s_id = reinterpret_cast<uint16_t*>(s_rp + N + 4);
+  float* s_sum = s_cl + 128;
+  int* s_rp = reinterpret_cast<int*>(s_sum + NC);
+  uint16_t* s_id = reinterpret_cast<uint16_t*>(s_rp + NC + 4);
   const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
 
   for (;;) {
@@ -196,27 +200,29 @@ __global__ void __launch_bounds__(kBatchMaxThreads) k_gn_batch(const BatchParams
           }
           if (row) { s_rh[q] = a.hi; s_rl[q] = a.lo; } else { s_ch[q] = a.hi; s_cl[q] = a.lo; }
         }
-        __syncthreads();
-        for (int i = tid; i < n; i += blockDim.x) {
+      }
+      __syncthreads();
+      // ---- update (assignment: the neighbour sum from the row and column sums, here)
+      const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
+      CheckAcc acc;
+      for (int i = tid; i < n; i += blockDim.x) {
+        dev::f2 y = {s_yh[i], s_yl[i]};
+        float x = s_x[i];
+        float sn;
+        if (kind == GN_INSTANCE_CSR) {
+          sn = s_sum[i];
+        } else {
           const int r = i / kk, c = i - r * kk;
-          const float yv = s_yh[i];
+          const float yv = y.hi;
           // (R_r - y) + (C_c - y) in float pairs
           dev::f2 a = dev::two_sum(s_rh[r], -yv);
           a.lo = dev::fadd(a.lo, s_rl[r]);
           dev::f2 b = dev::two_sum(s_ch[c], -yv);
           b.lo = dev::fadd(b.lo, s_cl[c]);
           const dev::f2 t = dev::two_sum(a.hi, b.hi);
-          s_sum[i] = dev::fadd(t.hi, dev::fadd(t.lo, dev::fadd(a.lo, b.lo)));
+          sn = dev::fadd(t.hi, dev::fadd(t.lo, dev::fadd(a.lo, b.lo)));
         }
-      }
-      __syncthreads();
-      // ---- update
-      const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
-      CheckAcc acc;
-      for (int i = tid; i < n; i += blockDim.x) {
-        dev::f2 y = {s_yh[i], s_yl[i]};
-        float x = s_x[i];
-        update_one(y, dev::f2{s_vh[i], s_vl[i]}, x, s_sum[i], gam, check, check ? P.w[v0 + i] : 0.0f, th_lo,
+        update_one(y, dev::f2{s_vh[i], s_vl[i]}, x, sn, gam, check, check ? P.w[v0 + i] : 0.0f, th_lo,
                    th_hi, hits, acc);
         s_yh[i] = y.hi;
         s_yl[i] = y.lo;
@@ -458,6 +464,7 @@ struct gn_batch {
   int count = 0;
   int64_t ntot = 0, etot = 0;
   int nmax = 0;
+  int ncsr = 0;
   int64_t* d_vtx_off = nullptr;
   int64_t* d_ent_off = nullptr;
   int32_t* d_rp = nullptr;
@@ -501,14 +508,14 @@ struct gn_batch {
 
 namespace gn {
 
-static size_t batch_smem(int nmax, int idcap) {
-  return sizeof(float) * (6 * (size_t)nmax + 4 * 128) + sizeof(int) * ((size_t)nmax + 4) +
+static size_t batch_smem(int nmax, int ncsr, int idcap) {
+  return sizeof(float) * (5 * (size_t)nmax + 4 * 128 + (size_t)ncsr) + sizeof(int) * ((size_t)ncsr + 4) +
          sizeof(uint16_t) * (size_t)idcap;
 }
 
 // CTA size -> CTAs per SM and the id capacity that still fits
 static gn_status batch_config(gn_batch* b, int threads) {
-  const size_t base = batch_smem(b->nmax, 0);
+  const size_t base = batch_smem(b->nmax, b->ncsr, 0);
   const size_t limit = 220 * 1024;
   if (base > limit) return fail(GN_ERR_TOO_LARGE, "gn_batch: largest instance exceeds shared memory");
   // prefer two CTAs per SM for 512 threads or fewer when the base layout allows it
@@ -519,7 +526,7 @@ static gn_status batch_config(gn_batch* b, int threads) {
     budget = limit;
   }
   const int idcap = (int)std::min<size_t>((budget - base) / sizeof(uint16_t), 1 << 20);
-  const size_t smem = batch_smem(b->nmax, idcap);
+  const size_t smem = batch_smem(b->nmax, b->ncsr, idcap);
   GN_CUDA(cudaFuncSetAttribute((const void*)k_gn_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit));
   int per_sm = 0;
   GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gn_batch, threads, smem));
@@ -600,6 +607,7 @@ extern "C" gn_status gn_batch_create(gn_batch** out, int32_t count, const int64_
       const double avg = (double)e / n;
       while (G < 32 && G * 3 < avg) G <<= 1;
       grp[i] = G;
+      b->ncsr = std::max<int>(b->ncsr, (int)n);
     } else {
       return fail(GN_ERR_ARG, "gn_batch_create: unknown instance kind");
     }
@@ -722,6 +730,7 @@ static gn_status batch_enqueue(gn_batch* b, const float* x0_dev, int max_iters, 
   P.theta = p.theta_bin;
   P.tol = tol;
   P.nmax = b->nmax;
+  P.ncsr = b->ncsr;
   P.idcap = b->idcap;
   k_gn_batch<<<b->ctas, b->threads, b->smem, b->stream>>>(P);
   GN_LAUNCHED();

@@ -160,3 +160,31 @@ def test_random_start_and_multi_start(gn):
         Wo = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)[3]
         assert abs(ws[s] - Wo) <= 1e-3 * Wo
     assert W == ws.max()
+
+
+def test_assignment_up_to_k96_in_one_launch(gn):
+    """The stress end of the batched config's assignment sizes: k = 96 (9216 vertices, 1.75M
+    entries in CSR form), 90 and 72 next to a CSR instance in one launch.  The structured form
+    keeps five state arrays per vertex in shared memory, so they fit; each instance follows the
+    oracle and ends on a permutation."""
+    specs = []
+    for i, k in enumerate((96, 90, 72)):
+        rng = inputs.rng_for(4000 + i)
+        cost = rng.random((k, k))
+        w = (2.0 - cost).astype(np.float32).reshape(-1)
+        specs.append(("assignment", k, w, (2.0 - w.astype(np.float64)).reshape(k, k)))
+    specs.append(inputs.er_graph(3000, 10.0, 4010))
+    b = gn.Batch(batch_items(specs))
+    run_kw, pk = fixed_steps(20)
+    x, infos = b.run(params=gn.default_params(**pk), **run_kw)
+    for s, xi, inf in zip(specs, split(x, b.vtx_off), infos):
+        inst = as_csr(s)
+        xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, p=oracle.params(**pk), **run_kw)
+        assert inf["iters"] == 20
+        assert_close_rel(xi, xo)
+    x, infos = b.run(max_iters=2000, tol=1e-7)
+    for s, xi, inf in zip(specs, split(x, b.vtx_off), infos):
+        assert inf["status"] == "OK"
+        if isinstance(s, tuple):
+            P = (xi > 0.5).reshape(s[1], s[1])
+            assert np.all(P.sum(0) == 1) and np.all(P.sum(1) == 1)
