@@ -57,6 +57,9 @@ struct BatchParams {
   int check_every;
   double theta;
   double tol;
+  float thr_hi, thr_lo;     // gamma (1 - theta) > theta <=> gamma > thr (float pair), no FP64
+  float tol_f;              // r <= tol <=> r <= tol_f for an FP32 r
+  int res_test;             // tol >= 0
   int nmax;                 // largest instance (the state arrays of the shared-memory layout)
   int ncsr;                 // largest CSR instance (its neighbour sums and row offsets)
   int idcap;                // local ids held in shared memory up to this many entries
@@ -233,9 +236,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
         const float r = block_max_f(acc.rmax, s_rf);
         const unsigned nb = block_sum_u(acc.nonbin, s_ru);
         const dev::f2 ob = block_sum_pair(dev::f2{acc.obj, 0.0f}, s_ph, s_pl);
-        const double gd = (double)gg.x + (double)gg.y;
-        const bool bin_ok = nb == 0u && gd * (1.0 - P.theta) > P.theta;
-        const bool res_ok = P.tol >= 0.0 && (double)r <= P.tol;
+        const dev::f2 dg = dev::two_sum(gg.x, -P.thr_hi);
+        const bool bin_ok = nb == 0u && dev::fadd(dg.hi, dev::fadd(dg.lo, dev::fsub(gg.y, P.thr_lo))) > 0.0f;
+        const bool res_ok = P.res_test && r <= P.tol_f;
         last_r = r;
         last_n = nb;
         last_obj = ob;
@@ -729,6 +732,15 @@ static gn_status batch_enqueue(gn_batch* b, const float* x0_dev, int max_iters, 
   P.check_every = p.check_every;
   P.theta = p.theta_bin;
   P.tol = tol;
+  {
+    const double thr = p.theta_bin / (1.0 - p.theta_bin);
+    P.thr_hi = (float)thr;
+    P.thr_lo = (float)(thr - (double)P.thr_hi);
+    P.res_test = tol >= 0.0 ? 1 : 0;
+    float f = (float)tol;
+    if ((double)f > tol) f = std::nextafter(f, -INFINITY);
+    P.tol_f = f;
+  }
   P.nmax = b->nmax;
   P.ncsr = b->ncsr;
   P.idcap = b->idcap;

@@ -136,20 +136,50 @@ __global__ void k_members_count(int n, const uint8_t* __restrict__ mask_int,
 }
 
 // exclusive scan of the per-CTA counts (one CTA, sequential per thread chunk) + W(S) total
-__global__ void k_scan_counts(int nb, int* __restrict__ bcount, int* __restrict__ total,
-                              const double* __restrict__ bsum, double* __restrict__ wtotal) {
-  if (threadIdx.x == 0) {
-    int run = 0;
-    double ws = 0.0;
-    for (int j = 0; j < nb; ++j) {
-      int c = bcount[j];
-      bcount[j] = run;
-      run += c;
-      ws += bsum[j];
-    }
-    *total = run;
-    *wtotal = ws;
+// exclusive prefix of the per-block member counts (in place) and their total, and the total
+// weight (FP64 sum of the per-block partials).  One CTA: each thread takes a contiguous chunk,
+// then a block scan of the chunk counts (the FP64 adds run in parallel, not as one chain).
+__global__ void __launch_bounds__(1024) k_scan_counts(int nb, int* __restrict__ bcount, int* __restrict__ total,
+                                                      const double* __restrict__ bsum,
+                                                      double* __restrict__ wtotal) {
+  __shared__ int s_warp[32];
+  __shared__ double sh[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+  const int C = (nb + blockDim.x - 1) / blockDim.x;
+  const int a = min(nb, t * C), b = min(nb, a + C);
+  int cnt = 0;
+  double ws = 0.0;
+  for (int j = a; j < b; ++j) {
+    cnt += bcount[j];
+    ws += bsum[j];
   }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int v = lane < nwarps ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    s_warp[lane] = v;  // inclusive totals of warps 0..lane
+  }
+  __syncthreads();
+  int run = incl - cnt + (warp > 0 ? s_warp[warp - 1] : 0);
+  for (int j = a; j < b; ++j) {
+    const int c = bcount[j];
+    bcount[j] = run;
+    run += c;
+  }
+  if (t == (int)blockDim.x - 1) *total = run;
+  const double tw = block_sum_d(ws, sh);
+  if (t == 0) *wtotal = tw;
 }
 
 __global__ void k_members_write(int n, const uint8_t* __restrict__ mask_c, const int* __restrict__ boff,
@@ -256,7 +286,7 @@ extern "C" gn_status gn_extract_is(gn_graph* g, const float* x, uint8_t* mask, i
   k_members_count<<<nbk, T, 0, g->stream>>>(n, g->d_mask, g->d_iperm, g->d_w, g->d_mask_c,
                                             g->d_bcount, g->d_bws);
   GN_LAUNCHED();
-  k_scan_counts<<<1, 32, 0, g->stream>>>(nbk, g->d_bcount, ctot, g->d_bws, g->d_red);
+  k_scan_counts<<<1, 1024, 0, g->stream>>>(nbk, g->d_bcount, ctot, g->d_bws, g->d_red);
   GN_LAUNCHED();
   k_members_write<<<nbk, T, 0, g->stream>>>(n, g->d_mask_c, g->d_bcount, g->d_members);
   GN_LAUNCHED();

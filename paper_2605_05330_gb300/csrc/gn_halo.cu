@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   // prologue: the starting states into inbox[0] (push), then every CTA's halo is complete
   if (PUSH) push_states(piece, H.npiece, ssrc, s_all, P.inbox);
   if (P.iterflag) {
-    if (publish_and_stop(P, false, slot, false, 0.0, k - 1, T) == 2) stop = 2;
+    if (publish_and_stop(P, false, slot, false, dev::f2{0.0f, 0.0f}, k - 1, T) == 2) stop = 2;
   } else {
     ++nbar;
     if (!dev::grid_barrier(P.bar, nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u), P.status,
@@ -285,7 +285,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
 
   for (; stop != 2 && k < P.k_end; ++k) {
     const int r = k - P.k_start;
-    const double gam_d = T.gd;
     const dev::f2 gam = {T.gh, T.gl};
     const float2 gnext = gamma_fetch(P, k + 1);
     const float* inbox_in = PUSH ? P.inbox + (size_t)(r & 1) * (size_t)P.inbox_len : nullptr;
@@ -387,8 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       push_states(piece, H.npiece, ssrc, s_all, inbox_out);
     }
     // 6. synchronisation and the stop decision
-    stop = P.iterflag ? publish_and_stop(P, fail, slot, check, gam_d, k, T)
-                      : barrier_and_stop(P, PUSH, fail, nbar, slot, check, gam_d, k, T);
+    stop = P.iterflag ? publish_and_stop(P, fail, slot, check, gam, k, T)
+                      : barrier_and_stop(P, PUSH, fail, nbar, slot, check, gam, k, T);
     synced = check;
     if (stop == 2) break;
     parity ^= 1;

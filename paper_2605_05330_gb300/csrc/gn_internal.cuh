@@ -41,13 +41,14 @@ enum DevStatus : int {
   DEV_BAD_WEIGHT = 16,
 };
 
-// per-CTA partial of a stop-test check (double-buffered by check parity)
+// per-CTA partial of a stop-test check (double-buffered by check parity).  The sums are float
+// pairs (hi + lo): FP64 arithmetic is slow on this GPU and stays off the iteration path.
 struct alignas(32) CheckPartial {
   float rmax;           // max |x' - x|
   unsigned nonbin;      // count of theta < x' < 1 - theta
-  double l1;            // sum |x' - x|
-  double obj;           // sum w x'
-  double energy;        // sum y (d/2 - v)  (E~ of the state entering the step)
+  float l1h, l1l;       // sum |x' - x|
+  float objh, objl;     // sum w x'
+  float enh, enl;       // sum y (d/2 - v)  (E~ of the state entering the step)
 };
 
 // summary the iteration kernels leave on the device (one D2H copy per run)

@@ -36,6 +36,12 @@ struct IterParams {
   int check_every;
   double theta;
   double tol;
+  // the stop test without FP64 on the device: gamma (1 - theta) > theta as gamma > thr, thr =
+  // theta / (1 - theta) as a float pair; the residual test as r <= tol_f, tol_f the largest
+  // float <= tol (exact for an FP32 r), on when res_test
+  float thr_hi, thr_lo;
+  float tol_f;
+  int res_test;
   int heavy;
   int rows_pad;
   int halo_pad;
@@ -132,8 +138,7 @@ __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, 
 }
 
 struct TailShared {
-  float gh, gl;     // gamma_k of the coming iteration as a float pair, and in FP64
-  double gd;
+  float gh, gl;     // gamma_k of the coming iteration as a float pair
   float rf[32];
   unsigned ru[32];
   float rdh[3][32];
@@ -176,9 +181,12 @@ __device__ __forceinline__ void write_check_partial(const IterParams& P, const C
       CheckPartial cp;
       cp.rmax = r2;
       cp.nonbin = n2;
-      cp.l1 = (double)q[0].hi + (double)q[0].lo;
-      cp.obj = (double)q[1].hi + (double)q[1].lo;
-      cp.energy = (double)q[2].hi + (double)q[2].lo;
+      cp.l1h = q[0].hi;
+      cp.l1l = q[0].lo;
+      cp.objh = q[1].hi;
+      cp.objl = q[1].lo;
+      cp.enh = q[2].hi;
+      cp.enl = q[2].lo;
       P.partials[slot * P.nblocks + blockIdx.x] = cp;
     }
   }
@@ -187,7 +195,18 @@ __device__ __forceinline__ void write_check_partial(const IterParams& P, const C
 // The stop test after every CTA's partial of check slot `slot` is visible: every CTA reduces
 // the same partials in the same order, so all take the same decision.  Returns 0 (continue)
 // or 1 (stop after this iteration).
-__device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, double gam_d, int k, TailShared& T) {
+// gamma > thr for float pairs (the binarity condition gamma (1 - theta) > theta)
+__device__ __forceinline__ bool gamma_above(const IterParams& P, dev::f2 gam) {
+  const dev::f2 d = dev::two_sum(gam.hi, -P.thr_hi);
+  return dev::fadd(d.hi, dev::fadd(d.lo, dev::fsub(gam.lo, P.thr_lo))) > 0.0f;
+}
+// float-pair accumulation a += (hi, lo)
+__device__ __forceinline__ void add_pair(dev::f2& a, float hi, float lo) {
+  const dev::f2 s = dev::two_sum(a.hi, hi);
+  a = dev::fast_two_sum(s.hi, dev::fadd(s.lo, dev::fadd(a.lo, lo)));
+}
+
+__device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, dev::f2 gam, int k, TailShared& T) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const CheckPartial* cps = P.partials + slot * P.nblocks;
   float fr = 0.0f;
@@ -210,23 +229,24 @@ __device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, dou
       tr = fmaxf(tr, T.rf[j]);
       tn += T.ru[j];
     }
-    const bool bin_ok = (tn == 0u) && (gam_d * (1.0 - P.theta) > P.theta);
-    const bool res_ok = P.tol >= 0.0 && (double)tr <= P.tol;
+    const bool bin_ok = (tn == 0u) && gamma_above(P, gam);
+    const bool res_ok = P.res_test && tr <= P.tol_f;
     const int stop = (bin_ok || res_ok) ? 1 : 0;
     T.decide = stop;
     if (blockIdx.x == 0 && (stop || k + 1 == P.k_end)) {
-      // FP64 summary of the final step, block 0 only, fixed order
-      double a2 = 0.0, o2 = 0.0, q2 = 0.0;
+      // summary of the final step, block 0 only, fixed order, float pairs (one FP64 rounding
+      // per quantity at the end)
+      dev::f2 a2 = {0.0f, 0.0f}, o2 = {0.0f, 0.0f}, q2 = {0.0f, 0.0f};
       for (int j = 0; j < P.nblocks; ++j) {
-        a2 += __ldcg(&cps[j].l1);
-        o2 += __ldcg(&cps[j].obj);
-        q2 += __ldcg(&cps[j].energy);
+        add_pair(a2, __ldcg(&cps[j].l1h), __ldcg(&cps[j].l1l));
+        add_pair(o2, __ldcg(&cps[j].objh), __ldcg(&cps[j].objl));
+        add_pair(q2, __ldcg(&cps[j].enh), __ldcg(&cps[j].enl));
       }
       P.info->resid_inf = tr;
       P.info->nonbin = tn;
-      P.info->resid_l1 = a2;
-      P.info->objective = o2;
-      P.info->energy = q2;
+      P.info->resid_l1 = (double)a2.hi + (double)a2.lo;
+      P.info->objective = (double)o2.hi + (double)o2.lo;
+      P.info->energy = (double)q2.hi + (double)q2.lo;
       P.info->binary = tn == 0u;
       P.info->converged = stop;
     }
@@ -241,12 +261,12 @@ __device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, dou
 // whether the kernel has such waits.  Returns 0 (continue), 1 (stop after this iteration) or 2
 // (a wait hit its limit).
 __device__ __forceinline__ int barrier_and_stop(const IterParams& P, bool may_fail, bool fail, unsigned& nbar,
-                                                int& slot, bool check, double gam_d, int k, TailShared& T) {
+                                                int& slot, bool check, dev::f2 gam, int k, TailShared& T) {
   ++nbar;
   const unsigned target = nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u);
   if (!dev::grid_barrier(P.bar, target, P.status, P.spin_limit, may_fail, fail)) return 2;
   if (!check) return 0;
-  return stop_decision(P, slot, gam_d, k, T);
+  return stop_decision(P, slot, gam, k, T);
 }
 
 // Neighbour synchronisation, end of iteration k (k = k_start - 1: the prologue): once every
@@ -257,7 +277,7 @@ __device__ __forceinline__ int barrier_and_stop(const IterParams& P, bool may_fa
 // all flags first.  `fail` is this thread's record of a wait that hit its limit earlier in the
 // iteration.  Returns 0, 1 or 2 like barrier_and_stop.
 __device__ __forceinline__ int publish_and_stop(const IterParams& P, bool fail, int& slot, bool check,
-                                                double gam_d, int k, TailShared& T) {
+                                                dev::f2 gam, int k, TailShared& T) {
   __shared__ int s_ok;
   if (__syncthreads_or(fail)) return 2;
   const unsigned done = (unsigned)(k + 2 - P.k_start);
@@ -270,7 +290,7 @@ __device__ __forceinline__ int publish_and_stop(const IterParams& P, bool fail, 
   }
   __syncthreads();
   if (!s_ok) return 2;
-  return stop_decision(P, slot, gam_d, k, T);
+  return stop_decision(P, slot, gam, k, T);
 }
 
 // gamma_k (Sec. 6) for iteration k from the per-run table (float pair; FP64 value = hi + lo),
@@ -284,7 +304,6 @@ __device__ __forceinline__ void gamma_store(float2 g, TailShared& T) {
   if (threadIdx.x == 0) {
     T.gh = g.x;
     T.gl = g.y;
-    T.gd = (double)g.x + (double)g.y;
   }
 }
 __device__ __forceinline__ void set_gamma(const IterParams& P, int k, TailShared& T) {

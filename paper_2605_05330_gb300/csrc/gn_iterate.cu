@@ -89,7 +89,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   const int grp = tid / G, gl = tid & (G - 1), ngrp = blockDim.x / G;
 
   for (; k < P.k_end; ++k) {
-    const double gam_d = T.gd;
     const dev::f2 gam = {T.gh, T.gl};
     const float2 gnext = gamma_fetch(P, k + 1);
     const float* __restrict__ yin = parity ? P.y1 : P.y0;
@@ -129,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
     update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
     gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
     if (check) write_check_partial(P, acc, slot, T);
-    stop = barrier_and_stop(P, false, false, nbar, slot, check, gam_d, k, T);
+    stop = barrier_and_stop(P, false, false, nbar, slot, check, gam, k, T);
     if (stop == 2) break;
     parity ^= 1;
     if (stop) {
@@ -331,6 +330,21 @@ gn_status init_state(gn_graph* g, const float* x0_dev) {
   return GN_OK;
 }
 
+// The stop test's thresholds for the device (which does it without FP64): gamma (1 - theta) >
+// theta <=> gamma > theta / (1 - theta) (theta < 1/2), that threshold as a float pair; the
+// residual test r <= tol for an FP32 r <=> r <= the largest float <= tol.
+void set_stop_thresholds(IterParams& P, double theta, double tol) {
+  P.theta = theta;
+  P.tol = tol;
+  const double thr = theta / (1.0 - theta);
+  P.thr_hi = (float)thr;
+  P.thr_lo = (float)(thr - (double)P.thr_hi);
+  P.res_test = tol >= 0.0 ? 1 : 0;
+  float f = (float)tol;
+  if ((double)f > tol) f = std::nextafter(f, -INFINITY);
+  P.tol_f = f;
+}
+
 // Runs iterations k_start..k_end-1 from d_y[parity0] / d_x; the caller has zeroed d_info
 // except for a start-state status.  Fills *out from the device summary.
 gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const gn_params& p,
@@ -362,8 +376,7 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.gamma1 = p.gamma1;
   P.ramp = p.ramp_iters;
   P.check_every = p.check_every;
-  P.theta = p.theta_bin;
-  P.tol = tol;
+  set_stop_thresholds(P, p.theta_bin, tol);
   P.heavy = g->heavy;
   P.rows_pad = g->mode == MODE_HALO ? g->rows_pad_halo : ((g->max_rows + 3) & ~3);
   P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
@@ -778,8 +791,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     P.gamma1 = p.gamma1;
     P.ramp = p.ramp_iters;
     P.check_every = p.check_every;
-    P.theta = p.theta_bin;
-    P.tol = tol;
+    set_stop_thresholds(P, p.theta_bin, tol);
     P.heavy = 16 * G;
     P.rows_pad = R;
     P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);

@@ -325,14 +325,16 @@ __global__ void __launch_bounds__(kHeadRows) k_head(int n, const float* __restri
       dq[i] = (p - t) / (float)n;
     }
   }
-  // block sum of the loss (FP64, one atomic per CTA)
-  l = dev::warp_sum_d(l);
-  if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = l;
-  __syncthreads();
-  if (threadIdx.x == 0 && target) {
-    double s = 0.0;
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += sl[j];
-    atomicAdd(loss, s / (double)n);
+  // block sum of the loss (FP64, one atomic per CTA), training only (`target` is uniform)
+  if (target) {
+    l = dev::warp_sum_d(l);
+    if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += sl[j];
+      atomicAdd(loss, s / (double)n);
+    }
   }
 }
 
