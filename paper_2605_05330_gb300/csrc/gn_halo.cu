@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   unsigned long long hits = 0;
   int parity = 0, slot = 0, stop = 0;
   unsigned nbar = 0;
+  int nchk = 0;  // checks so far (grid mode: selects the check word)
   unsigned mphase = 0;  // parity of the mbarrier phase the next copy completes
   int k = P.k_start;
 
@@ -379,15 +380,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       update_rows(S, nr, rb, P.w, PUSH ? nullptr : yout, gam, check, th_lo, th_hi, hits, acc);
     }
     gamma_store(gnext, T);  // visible to every thread after the next __syncthreads
-    if (check) write_check_partial(P, acc, slot, T);
+    if (check && P.iterflag) write_check_partial(P, acc, slot, T);
     // 5. the new own states into the other CTAs' inboxes
     if (PUSH) {
       __syncthreads();
       push_states(piece, H.npiece, ssrc, s_all, inbox_out);
     }
-    // 6. synchronisation and the stop decision
-    stop = P.iterflag ? publish_and_stop(P, fail, slot, check, gam, k, T)
-                      : barrier_and_stop(P, PUSH, fail, nbar, slot, check, gam, k, T);
+    // 6. synchronisation and the stop decision (grid mode: at a check, fused into the barrier)
+    if (P.iterflag)
+      stop = publish_and_stop(P, fail, slot, check, gam, k, T);
+    else if (check)
+      stop = check_barrier(P, PUSH, fail, nbar, nchk, gam, k, acc, T);
+    else
+      stop = barrier_and_stop(P, PUSH, fail, nbar, slot, false, gam, k, T);
     synced = check;
     if (stop == 2) break;
     parity ^= 1;

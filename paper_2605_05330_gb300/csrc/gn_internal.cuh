@@ -121,7 +121,7 @@ struct gn_graph {
   float* d_tmp = nullptr;       // internal-order scratch state
   double* d_bsum = nullptr;     // per-CTA FP64 partial sums of the small reductions
   gn::CheckPartial* d_partials = nullptr;  // [2][nblocks]
-  unsigned* d_bar = nullptr;
+  unsigned* d_bar = nullptr;   // [8]: grid-barrier counter, then three 64-bit check words (bytes 8..31)
   unsigned* d_iterflag = nullptr;  // [kFlagStride * nblocks] per-CTA push counts (halo mode)
   float* d_inbox = nullptr;        // [2][inbox_len] halo inboxes (halo mode, push exchange)
   bool halo_push = false;          // halo mode: push exchange (else pull)
@@ -195,6 +195,17 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;

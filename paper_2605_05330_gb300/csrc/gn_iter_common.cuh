@@ -256,6 +256,92 @@ __device__ __forceinline__ int stop_decision(const IterParams& P, int& slot, dev
   return T.decide;
 }
 
+// The run's summary at its final check (stop, or the last iteration): every CTA writes its full
+// partial (slot 0), one more grid barrier, then block 0 reduces the partials in a fixed order
+// (float pairs; one FP64 rounding per quantity) and writes the summary.  False if a wait hit
+// its limit.
+__device__ __forceinline__ bool final_summary(const IterParams& P, unsigned& nbar, const CheckAcc& acc, int stop,
+                                              TailShared& T) {
+  write_check_partial(P, acc, 0, T);
+  ++nbar;
+  if (!dev::grid_barrier(P.bar, nbar * (unsigned)P.nblocks + (P.unreachable ? 1u : 0u), P.status, P.spin_limit))
+    return false;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float tr = 0.0f;
+    unsigned tn = 0;
+    dev::f2 a2 = {0.0f, 0.0f}, o2 = {0.0f, 0.0f}, q2 = {0.0f, 0.0f};
+    for (int j = 0; j < P.nblocks; ++j) {
+      const CheckPartial* c = P.partials + j;
+      tr = fmaxf(tr, __ldcg(&c->rmax));
+      tn += __ldcg(&c->nonbin);
+      add_pair(a2, __ldcg(&c->l1h), __ldcg(&c->l1l));
+      add_pair(o2, __ldcg(&c->objh), __ldcg(&c->objl));
+      add_pair(q2, __ldcg(&c->enh), __ldcg(&c->enl));
+    }
+    P.info->resid_inf = tr;
+    P.info->nonbin = tn;
+    P.info->resid_l1 = (double)a2.hi + (double)a2.lo;
+    P.info->objective = (double)o2.hi + (double)o2.lo;
+    P.info->energy = (double)q2.hi + (double)q2.lo;
+    P.info->binary = tn == 0u;
+    P.info->converged = stop;
+  }
+  return true;
+}
+
+// The stop test fused into the grid barrier (checks in grid-barrier mode).  A CTA brings two
+// flags -- one of its rows is non-binary, one of its residuals is above tol -- and its arrival
+// on one of three rotating 64-bit check words adds 1 (bits 0..20, arrivals), the first flag
+// (bits 21..41) and the second (bits 42..62).  The poll that sees every arrival reads the two
+// counts with it, so all CTAs take the same decision with no further global reads: stop when
+// no CTA has a non-binary row and gamma (1 - theta) > theta, or when no residual exceeds tol.
+// Block 0 clears the previous check's word (every CTA read it before arriving here); that word
+// is used again three checks later, after barriers block 0 crosses only after clearing it.
+// Returns 0 (continue), 1 (stop after this iteration) or 2 (a wait hit its limit).
+__device__ __forceinline__ int check_barrier(const IterParams& P, bool may_fail, bool fail, unsigned& nbar,
+                                             int& nchk, dev::f2 gam, int k, const CheckAcc& acc, TailShared& T) {
+  __shared__ int s_ok;
+  const bool nb_any = __syncthreads_or(acc.nonbin != 0u) != 0;
+  const bool rf_any = __syncthreads_or(acc.rmax > P.tol_f) != 0;
+  if (may_fail && __syncthreads_or(fail)) return 2;
+  unsigned long long* words = reinterpret_cast<unsigned long long*>(P.bar + 2);
+  const int w = nchk % 3;
+  if (threadIdx.x == 0) {
+    constexpr unsigned long long kField = (1ull << 21) - 1ull;
+    dev::red_release_add_u64(words + w, 1ull | (nb_any ? 1ull << 21 : 0ull) | (rf_any ? 1ull << 42 : 0ull));
+    const unsigned long long need = (unsigned long long)P.nblocks + (P.unreachable ? 1ull : 0ull);
+    int ok = 1;
+    long long spins = 0;
+    unsigned long long v;
+    while (((v = dev::ld_acquire_u64(words + w)) & kField) < need) {
+      ++spins;
+      if ((spins & 255) == 0 && dev::ld_relaxed_int(P.status) != 0) { ok = 0; break; }
+      if (spins > P.spin_limit) {
+        atomicOr(P.status, DEV_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    int stop = 0;
+    if (ok) {
+      const bool bin_ok = ((v >> 21) & kField) == 0ull && gamma_above(P, gam);
+      const bool res_ok = P.res_test && ((v >> 42) & kField) == 0ull;
+      stop = (bin_ok || res_ok) ? 1 : 0;
+      if (blockIdx.x == 0) dev::st_relaxed_u64(words + (w + 2) % 3, 0ull);
+    }
+    s_ok = ok;
+    T.decide = stop;
+  }
+  __syncthreads();
+  if (!s_ok) return 2;
+  ++nchk;
+  const int stop = T.decide;
+  if (stop || k + 1 == P.k_end) {
+    if (!final_summary(P, nbar, acc, stop, T)) return 2;
+  }
+  return stop;
+}
+
 // Grid barrier, then (at a check) the stop test.  `fail` is this thread's record of a wait
 // that hit its limit earlier in the iteration; `may_fail` (a constant at the call site) says
 // whether the kernel has such waits.  Returns 0 (continue), 1 (stop after this iteration) or 2

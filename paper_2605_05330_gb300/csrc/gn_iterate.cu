@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   unsigned long long hits = 0;
   int parity = 0, slot = 0, stop = 0;
   unsigned nbar = 0;
+  int nchk = 0;  // checks so far (selects the check word)
   int k = P.k_start;
   const int grp = tid / G, gl = tid & (G - 1), ngrp = blockDim.x / G;
 
@@ -127,8 +128,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
     CheckAcc acc;
     update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
     gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
-    if (check) write_check_partial(P, acc, slot, T);
-    stop = barrier_and_stop(P, false, false, nbar, slot, check, gam, k, T);
+    stop = check ? check_barrier(P, false, false, nbar, nchk, gam, k, acc, T)
+                 : barrier_and_stop(P, false, false, nbar, slot, false, gam, k, T);
     if (stop == 2) break;
     parity ^= 1;
     if (stop) {
@@ -402,7 +403,7 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.gtab_len = glen;
   KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo, g->halo_push)
                                      : pick_kernel(g->group, g->mode);
-  GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned), g->stream));
+  GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 8, g->stream));  // counter and check words
   if (P.iterflag)
     GN_CUDA(cudaMemsetAsync(g->d_iterflag, 0, sizeof(unsigned) * dev::kFlagStride * g->nblocks, g->stream));
   void* args[] = {(void*)&P};
@@ -741,7 +742,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
 
   // what must start at zero: the run summary (status, counters) and the barrier counter
   GN_CUDA(cudaMemsetAsync(s_info, 0, sizeof(DevInfo), stream));
-  GN_CUDA(cudaMemsetAsync(s_bar, 0, sizeof(unsigned), stream));
+  GN_CUDA(cudaMemsetAsync(s_bar, 0, sizeof(unsigned) * 8, stream));  // counter and check words
   const unsigned grid = (unsigned)std::max(n, nb + 1);
   k_na_check_rows<<<(n + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, &s_info->status);
   GN_LAUNCHED();
