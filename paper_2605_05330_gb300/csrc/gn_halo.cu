@@ -2,11 +2,12 @@
 //
 // Each CTA owns a contiguous range of rows for the whole run and keeps everything it needs
 // in shared memory:
-//   s_all  = [ own weighted states y_i (hi parts) | external halo values | one zero ]
+//   s_all  = [ own weighted states y_i (hi parts) | external halo values | 32 zeros ]
 //   a packed per-CTA block (built once on the host): the light rows in SELL-32 slices
 //   (32 rows per slice, a lane per row, 16-bit local ids into s_all packed four per lane in
-//   8-byte words, rows sorted interior-first then by degree, each column's entries spread
-//   over the shared-memory banks), the heavy rows cut into chunks of at most 256 entries
+//   8-byte words, rows sorted interior-first then by degree; each column is one gather
+//   instruction and touches 32 distinct banks, see color_slice), the heavy rows cut into
+//   chunks of at most 256 entries
 //   (a warp per chunk; a row's chunk sums are added in chunk order, so the result does not
 //   depend on which warp took which chunk) and the CTA's send list.
 //
@@ -59,7 +60,7 @@ struct HaloHeader {
   int lx;          // external halo length
   int sell_len;    // SELL entries (with padding)
   int heavy_len;   // local ids of the heavy rows
-  int zero_id;     // local id of the zero slot (padding)
+  int zero_id;     // local id of the first of 32 zero slots, one per bank (padding)
   int inbox_off;   // float offset of this CTA's inbox in one inbox buffer (multiple of 4)
   int off_meta;    // byte offsets of the sections from the block start
   int off_srow;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   if (dev::ld_relaxed_int(P.status) != 0) return;
 
   float* s_all = reinterpret_cast<float*>(smem);
-  const int nall = R + P.halo_pad + 4;
+  const int nall = R + P.halo_pad + 32;
   RowArrays S;
   S.yh = s_all;
   S.sum = s_all + nall;
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   const int4* __restrict__ piece = reinterpret_cast<const int4*>(blk + H.off_piece);
   const uint16_t* __restrict__ ssrc = reinterpret_cast<const uint16_t*>(blk + H.off_src);
   const int* __restrict__ xlist = reinterpret_cast<const int*>(blk + H.off_x);
-  if (tid == 0) s_all[H.zero_id] = 0.0f;
+  if (tid < 32) s_all[H.zero_id + tid] = 0.0f;  // one zero slot per bank (padding)
   set_gamma(P, P.k_start, T);
   float* s_halo = s_all + R;
   const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
@@ -430,6 +431,68 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
 
 static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+// Bank-conflict-free SELL columns.  In a slice, lane l's row has its entries (local ids, bank
+// = id mod 32) and column c of the slice is one gather instruction over the 32 lanes.  The
+// entries form a bipartite multigraph lanes x banks; colouring its edges with W colours so
+// that no two edges at a lane or at a bank share a colour puts every lane's entries in
+// distinct columns and every column's entries in distinct banks.  W colours suffice when W >=
+// every lane's degree and every bank's load (Konig's edge-colouring theorem).  Alternating-path
+// method: for an edge (l, b) take a colour a free at l and a
+// colour c free at b; if a is also free at b use it, else swap a and c along the path from b
+// whose edges alternate a, c, a, ... -- that frees a at b and cannot reach l, which has no
+// a-edge.  lid[l] lists lane l's ids; the result col[l][k] is the column of lid[l][k].
+static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int>* col,
+                        std::vector<int>& at_l, std::vector<int>& at_b, std::vector<int>& elane,
+                        std::vector<int>& ebank, std::vector<int>& ecol, std::vector<int>& path) {
+  at_l.assign(32 * (size_t)W, -1);
+  at_b.assign(32 * (size_t)W, -1);
+  elane.clear();
+  ebank.clear();
+  ecol.clear();
+  for (int l = 0; l < 32; ++l) {
+    for (size_t k = 0; k < lid[l].size(); ++k) {
+      const int e = (int)elane.size(), b = lid[l][k] & 31;
+      elane.push_back(l);
+      ebank.push_back(b);
+      ecol.push_back(-1);
+      int a = 0, c = 0;
+      while (at_l[l * W + a] >= 0) ++a;
+      while (at_b[b * W + c] >= 0) ++c;
+      if (at_b[b * W + a] >= 0) {
+        // the a/c path from bank b
+        path.clear();
+        int v = b, cur = a;
+        bool bank_side = true;
+        for (;;) {
+          const int f = bank_side ? at_b[v * W + cur] : at_l[v * W + cur];
+          if (f < 0) break;
+          path.push_back(f);
+          v = bank_side ? elane[f] : ebank[f];
+          bank_side = !bank_side;
+          cur = cur == a ? c : a;
+        }
+        for (int f : path) {
+          at_l[elane[f] * W + ecol[f]] = -1;
+          at_b[ebank[f] * W + ecol[f]] = -1;
+        }
+        for (int f : path) {
+          ecol[f] = ecol[f] == a ? c : a;
+          at_l[elane[f] * W + ecol[f]] = f;
+          at_b[ebank[f] * W + ecol[f]] = f;
+        }
+      }
+      ecol[e] = a;
+      at_l[l * W + a] = e;
+      at_b[b * W + a] = e;
+    }
+  }
+  int e = 0;
+  for (int l = 0; l < 32; ++l) {
+    col[l].resize(lid[l].size());
+    for (size_t k = 0; k < lid[l].size(); ++k) col[l][k] = ecol[e++];
+  }
+}
+
 // A CTA's halo is "dense" when it averages at least this many values per 32-byte sector:
 // then the pull exchange reads few sectors and wins; below it the push exchange does.
 static constexpr double kPullDensity = 4.0;
@@ -580,6 +643,9 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       std::vector<int2> meta(ns);
       std::vector<short> srow((size_t)ns * 32, (short)-1);
       int sell_len = 0;
+      // slice width: the longest row (widening to the busiest bank's load, which would make
+      // every gather conflict-free, measured slower: the extra columns cost more than the
+      // conflicts they remove)
       for (int s = 0; s < ns; ++s) {
         int wmax = 0;
         for (int l = 0; l < 32; ++l) {
@@ -666,16 +732,19 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     blk_max = std::max(blk_max, blocks[b].size());
   }
   const int Lp = (lx_max + 3) & ~3;
-  const int zero_id = R + Lp;
-  const size_t floats = (size_t)6 * R + Lp + 4;
+  const int zero_id = R + Lp;  // 32 zero slots from here, one per bank
+  const size_t floats = (size_t)6 * R + Lp + 32;
   const size_t smem = 4 * floats + blk_max;
-  if (zero_id > 65535 || smem > smem_limit || R > 32767) return GN_OK;  // does not fit
+  if (zero_id + 31 > 65535 || smem > smem_limit || R > 32767) return GN_OK;  // does not fit
 
   // pass 2, per CTA: the 16-bit local ids (own row r -> r, external halo t -> R + t,
   // padding -> the zero slot)
   parallel_for(nb, 1, [&](int lo, int hi, int) {
     std::vector<int32_t> extpos(std::max(n, 1), 0);
-    std::vector<std::vector<uint16_t>> pending(32);
+    std::vector<uint16_t> lids[32];
+    std::vector<int> cols[32];
+    std::vector<int> at_l, at_b, elane, ebank, ecol, path, occ;
+    std::vector<uint16_t> bucket[32];
     for (int b = lo; b < hi; ++b) {
       const int rb = part[b], re = part[b + 1];
       std::vector<unsigned char>& B = blocks[b];
@@ -688,41 +757,79 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       const int2* meta = reinterpret_cast<const int2*>(B.data() + H->off_meta);
       const short* srow = reinterpret_cast<const short*>(B.data() + H->off_srow);
       uint16_t* sell = reinterpret_cast<uint16_t*>(B.data() + H->off_sell);
-      // Within a slice every lane's row may list its entries in any order.  Column by column,
-      // give each lane the unused entry whose shared-memory bank (local id mod 32) is least
-      // taken in that column, so the 32 lanes' gathers spread over the banks.
+      // Every lane's row may list its entries in any order: colour the slice (color_slice) so
+      // that each column's real entries lie in distinct banks, then pad each lane's empty
+      // columns with the zero slot of a bank no real entry of that column uses (all padding of
+      // a column reads that one address: a broadcast).
       for (int s = 0; s < H->ns; ++s) {
+        const int W = meta[s].y;
         for (int l = 0; l < 32; ++l) {
           const int r = srow[s * 32 + l];
-          pending[l].clear();
+          lids[l].clear();
           if (r >= 0)
-            for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) pending[l].push_back(lid(ci[e]));
+            for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) lids[l].push_back(lid(ci[e]));
         }
-        for (int k = 0; k < meta[s].y; ++k) {
-          int load[32] = {0};
+        // colours for the slice's busiest bank; when that is more than the slice's width, the
+        // colours past the width fold into each lane's free columns, least-used bank first
+        // (only those gathers can conflict)
+        int Wc = W, load[32] = {0};
+        for (int l = 0; l < 32; ++l)
+          for (uint16_t id : lids[l]) ++load[id & 31];
+        for (int t = 0; t < 32; ++t) Wc = std::max(Wc, load[t]);
+        color_slice(Wc, lids, cols, at_l, at_b, elane, ebank, ecol, path);
+        occ.assign(32 * (size_t)W, 0);  // occ[bank * W + column]
+        for (int l = 0; l < 32; ++l)
+          for (size_t t = 0; t < lids[l].size(); ++t)
+            if (cols[l][t] < W) ++occ[(lids[l][t] & 31) * W + cols[l][t]];
+        if (Wc > W) {
           for (int l = 0; l < 32; ++l) {
-            std::vector<uint16_t>& q = pending[l];
-            uint16_t pick = (uint16_t)zero_id;
-            if (!q.empty()) {
-              size_t best = 0;
-              for (size_t t = 1; t < q.size() && load[q[best] & 31]; ++t)
-                if (load[q[t] & 31] < load[q[best] & 31]) best = t;
-              pick = q[best];
-              q[best] = q.back();
-              q.pop_back();
-              ++load[pick & 31];
+            uint64_t used = 0;
+            for (size_t t = 0; t < lids[l].size(); ++t)
+              if (cols[l][t] < W) used |= 1ull << cols[l][t];
+            for (size_t t = 0; t < lids[l].size(); ++t) {
+              if (cols[l][t] < W) continue;
+              const int bk = lids[l][t] & 31;
+              int best = -1;
+              for (int k = 0; k < W; ++k)
+                if (!(used >> k & 1ull) && (best < 0 || occ[bk * W + k] < occ[bk * W + best])) best = k;
+              cols[l][t] = best;
+              used |= 1ull << best;
+              ++occ[bk * W + best];
             }
-            sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = pick;
           }
         }
+        for (int k = 0; k < W; ++k) {
+          int zb = 0;  // the bank least used by column k's real entries (unused when one exists)
+          for (int t = 1; t < 32; ++t)
+            if (occ[t * W + k] < occ[zb * W + k]) zb = t;
+          const uint16_t zero = (uint16_t)(zero_id + ((zb - zero_id) & 31));
+          for (int l = 0; l < 32; ++l) sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = zero;
+        }
+        for (int l = 0; l < 32; ++l)
+          for (size_t t = 0; t < lids[l].size(); ++t) {
+            const int k = cols[l][t];
+            sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = lids[l][t];
+          }
       }
       const int* hm = reinterpret_cast<const int*>(B.data() + H->off_hmeta);
       const int* hc = reinterpret_cast<const int*>(B.data() + H->off_hchunk);
       uint16_t* hl = reinterpret_cast<uint16_t*>(B.data() + H->off_hl);
+      // heavy rows: entries dealt round-robin over the banks, so each group of 32 consecutive
+      // entries (one gather instruction of sum_chunk) spreads over the banks
       for (int h = 0; h < H->nheavy; ++h) {
         const int r = hm[3 * h], o = hc[2 * hm[3 * h + 1]];  // the row's entries start at its first chunk
         const int d = rp[rb + r + 1] - rp[rb + r];
-        for (int k = 0; k < d; ++k) hl[o + k] = lid(ci[rp[rb + r] + k]);
+        size_t most = 0;
+        for (int t = 0; t < 32; ++t) bucket[t].clear();
+        for (int k = 0; k < d; ++k) {
+          const uint16_t id = lid(ci[rp[rb + r] + k]);
+          bucket[id & 31].push_back(id);
+        }
+        for (int t = 0; t < 32; ++t) most = std::max(most, bucket[t].size());
+        int k = 0;
+        for (size_t j = 0; j < most; ++j)
+          for (int t = 0; t < 32; ++t)
+            if (j < bucket[t].size()) hl[o + k++] = bucket[t][j];
       }
     }
   });
