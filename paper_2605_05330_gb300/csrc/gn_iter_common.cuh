@@ -125,15 +125,33 @@ __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, 
                                             float* __restrict__ yout, dev::f2 gam, bool check,
                                             float th_lo, float th_hi, unsigned long long& hits,
                                             CheckAcc& acc) {
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-    dev::f2 y = {S.yh[i], S.yl[i]};
-    float x = S.x[i];
-    update_one(y, dev::f2{S.vh[i], S.vl[i]}, x, S.sum[i], gam, check, check ? w[rb + i] : 0.0f, th_lo,
-               th_hi, hits, acc);
-    S.yh[i] = y.hi;
-    S.yl[i] = y.lo;
-    S.x[i] = x;
-    if (yout) yout[rb + i] = y.hi;
+  // rows i and i + blockDim.x together: their arithmetic has no branch between it, so the two
+  // dependency chains interleave (a row past the end computes on a fixed point and stores nothing)
+  const int step = blockDim.x;
+  for (int i = threadIdx.x; i < nr; i += 2 * step) {
+    const int i2 = i + step;
+    const bool in2 = i2 < nr;
+    const dev::f2 y1 = {S.yh[i], S.yl[i]};
+    const dev::f2 y2 = in2 ? dev::f2{S.yh[i2], S.yl[i2]} : dev::f2{1.0f, 0.0f};
+    const dev::f2 v1 = {S.vh[i], S.vl[i]};
+    const dev::f2 v2 = in2 ? dev::f2{S.vh[i2], S.vl[i2]} : dev::f2{1.0f, 0.0f};
+    const RowStep r1 = update_core(y1, v1, S.sum[i], gam);
+    const RowStep r2 = update_core(y2, v2, in2 ? S.sum[i2] : 0.0f, gam);
+    if (check) {
+      check_terms(r1, y1, v1, S.x[i], w[rb + i], th_lo, th_hi, acc);
+      if (in2) check_terms(r2, y2, v2, S.x[i2], w[rb + i2], th_lo, th_hi, acc);
+    }
+    hits += (r1.ok ? 0ull : 1ull) + (in2 && !r2.ok ? 1ull : 0ull);
+    S.yh[i] = r1.yn.hi;
+    S.yl[i] = r1.yn.lo;
+    S.x[i] = r1.xn.hi;
+    if (yout) yout[rb + i] = r1.yn.hi;
+    if (in2) {
+      S.yh[i2] = r2.yn.hi;
+      S.yl[i2] = r2.yn.lo;
+      S.x[i2] = r2.xn.hi;
+      if (yout) yout[rb + i2] = r2.yn.hi;
+    }
   }
 }
 
