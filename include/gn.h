@@ -72,7 +72,10 @@ typedef enum {
 
 #define GN_KERNEL_AUTO 0
 #define GN_KERNEL_PERSISTENT 1  /* multi-CTA persistent kernel with a bounded grid barrier */
-#define GN_KERNEL_CTA 2         /* whole graph in one CTA's shared memory */
+#define GN_KERNEL_CTA 2         /* whole graph in one CTA's shared memory (small graphs, up to
+                                   16384 vertices; no grid barrier).  A run from start_iter 0,
+                                   without record or resume; arithmetic of the global-gather
+                                   mode.  GN_KERNEL_AUTO is the persistent kernel. */
 
 typedef struct {
   int gamma_mode;       /* GN_GAMMA_PURSUIT (default) or GN_GAMMA_FIXED */
@@ -275,6 +278,8 @@ typedef struct {
   double resid_inf;     /* at the last check */
   double objective;     /* sum_i w_i x_i at the last check (float-pair sums, FP64 result) */
   long long safe_div_hits;
+  double resid_l1;      /* sum_i |x_i' - x_i| at the last check */
+  double energy;        /* E~ of the state entering the last check's step (Sec. 3) */
 } gn_batch_info;
 
 /*

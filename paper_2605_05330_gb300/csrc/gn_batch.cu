@@ -34,6 +34,8 @@ struct BatchInfoDev {
   float resid_inf;
   float pad;
   double objective;
+  double resid_l1;   // sum |x' - x| of the last check
+  double energy;     // E~ of the state entering the last check's step
 };
 
 struct BatchParams {
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
     float last_r = 0.0f;
     unsigned last_n = 0;
     dev::f2 last_obj = {0.0f, 0.0f};
+    float last_l1 = 0.0f, last_en = 0.0f;  // this thread's terms at the last check
     for (; k < P.k_end; ++k) {
       const float2 gg = P.gtab[k < P.gtab_len ? k : P.gtab_len - 1];
       const dev::f2 gam = {gg.x, gg.y};
@@ -242,6 +245,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
         last_r = r;
         last_n = nb;
         last_obj = ob;
+        last_l1 = acc.l1;
+        last_en = acc.en;
         if (bin_ok || res_ok) {
           stop = 1;
           ++k;
@@ -249,8 +254,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
         }
       }
     }
-    // ---- results
+    // ---- results (the last check's residual sum and energy: summed once, here)
     for (int i = tid; i < n; i += blockDim.x) P.x[v0 + i] = s_x[i];
+    const dev::f2 l1s = block_sum_pair(dev::f2{last_l1, 0.0f}, s_ph, s_pl);
+    const dev::f2 ens = block_sum_pair(dev::f2{last_en, 0.0f}, s_ph, s_pl);
     unsigned long long h = dev::warp_sum_ull(hits);
     __shared__ unsigned long long s_h[32];
     if (lane == 0) s_h[tid >> 5] = h;
@@ -267,6 +274,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
       bi.resid_inf = last_r;
       bi.pad = 0.0f;
       bi.objective = (double)last_obj.hi + (double)last_obj.lo;
+      bi.resid_l1 = (double)l1s.hi + (double)l1s.lo;
+      bi.energy = (double)ens.hi + (double)ens.lo;
       P.info[inst] = bi;
     }
     __syncthreads();
@@ -836,6 +845,8 @@ extern "C" gn_status gn_batch_run(gn_batch* b, const float* x0, int max_iters, d
       info[i].resid_inf = d.resid_inf;
       info[i].objective = d.objective;
       info[i].safe_div_hits = (long long)d.hits;
+      info[i].resid_l1 = d.resid_l1;
+      info[i].energy = d.energy;
     }
   }
   return (gn_status)worst;

@@ -214,10 +214,11 @@ extern "C" void gn_destroy(gn_graph* g) {
   cudaSetDevice(g->device);
   if (g->stream) cudaStreamSynchronize(g->stream);
   gn_free_record(g);
+  if (g->cta) gn_batch_destroy(g->cta);
   void* dptrs[] = {g->d_row_ptr, g->d_col_idx, g->d_w, g->d_v, g->d_vlo, g->d_ylo, g->d_perm, g->d_iperm, g->d_part,
                    g->d_y[0], g->d_y[1], g->d_x, g->d_tmp, g->d_bsum, g->d_io, g->d_partials, g->d_bar, g->d_iterflag, g->d_inbox, g->d_info,
                    g->d_flags, g->d_red, g->d_mask, g->d_mask_c, g->d_bcount, g->d_bws,
-                   g->d_members, g->d_hoff, g->d_hblob, g->d_gtab};
+                   g->d_members, g->d_hoff, g->d_hblob, g->d_gtab, g->d_cta_off};
   for (void* p : dptrs)
     if (p) cudaFree(p);
   if (g->h_info) cudaFreeHost(g->h_info);

@@ -142,6 +142,9 @@ struct gn_graph {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   gn::RecordState* rec = nullptr;          // checkpoints for gn_backward
+  gn_batch* cta = nullptr;                 // GN_KERNEL_CTA: a one-instance batch over this CSR
+  int64_t* d_cta_off = nullptr;            // its offsets (vertices, entries)
+  bool state_cta = false;                  // the last run was a CTA-kernel run (not resumable)
 };
 
 namespace gn {

@@ -419,6 +419,39 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   return GN_OK;
 }
 
+// GN_KERNEL_CTA: the whole run in one CTA, through a one-instance batch over the handle's CSR
+// (internal order, device-resident; built on first use).  The start state is d_x (written by
+// init_state) and the result goes back there.
+static gn_status run_cta(gn_graph* g, int max_iters, double tol, const gn_params& p, DevInfo* out, float* ms) {
+  if (!g->cta) {
+    const int64_t off[4] = {0, (int64_t)g->n, 0, g->nnz};
+    GN_CUDA(cudaMalloc(&g->d_cta_off, sizeof off));
+    GN_CUDA(cudaMemcpyAsync(g->d_cta_off, off, sizeof off, cudaMemcpyHostToDevice, g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+    gn_status st = gn_batch_create(&g->cta, 1, g->d_cta_off, g->d_cta_off + 2, g->d_row_ptr, g->d_col_idx,
+                                   g->d_w, nullptr, GN_DEVICE, g->stream);
+    if (st != GN_OK) {
+      g->cta = nullptr;
+      return st;
+    }
+  }
+  gn_batch_info bi;
+  gn_status st = gn_batch_run(g->cta, g->d_x, max_iters, tol, &p, g->d_x, &bi);
+  if (st < 0) return st;
+  memset(out, 0, sizeof *out);
+  out->iters = bi.iters;
+  out->converged = bi.converged;
+  out->binary = bi.binary;
+  out->nonbin = bi.binary ? 0u : 1u;  // the batch reports binarity, not the count
+  out->resid_inf = bi.resid_inf;
+  out->resid_l1 = bi.resid_l1;
+  out->objective = bi.objective;
+  out->energy = bi.energy;
+  out->hits = (unsigned long long)bi.safe_div_hits;
+  *ms = gn_batch_last_ms(g->cta);
+  return GN_OK;
+}
+
 }  // namespace gn
 
 // ------------------------------------------------------------------------------------------
@@ -438,8 +471,11 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
   GN_CUDA(cudaSetDevice(g->device));
   GN_CUDA(cudaMemsetAsync(g->d_info, 0, sizeof(DevInfo), g->stream));
   gn_status st = GN_OK;
+  if (p.kernel == GN_KERNEL_CTA && (p.resume || p.record || start_iter != 0))
+    return fail(GN_ERR_ARG, "gn_run: the CTA kernel runs whole runs (start_iter 0, no record or resume)");
   if (p.resume) {
     if (!g->has_state) return fail(GN_ERR_ARG, "gn_run: resume without a previous run on this handle");
+    if (g->state_cta) return fail(GN_ERR_ARG, "gn_run: the last run used the CTA kernel and cannot be resumed");
   } else {
     const float* x0_dev = nullptr;
     if (x0) {
@@ -470,6 +506,14 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
       di.binary = di.nonbin == 0;
       di.converged = di.binary && host_gamma(p, max_iters - 1) * (1.0 - p.theta_bin) > p.theta_bin;
     }
+  } else if (max_iters > start_iter && g->n > 0 && p.kernel == GN_KERNEL_CTA) {
+    GN_CUDA(cudaMemcpyAsync(&di, g->d_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, g->stream));
+    GN_CUDA(cudaStreamSynchronize(g->stream));
+    if (di.status == 0) {  // the start state passed init_state's checks
+      st = run_cta(g, max_iters, tol, p, &di, &ms);
+      if (st != GN_OK) return st;
+    }
+    kused = GN_KERNEL_CTA;
   } else if (max_iters > start_iter && g->n > 0) {
     st = run_iterations(g, start_iter, max_iters, tol, p, parity0, &di, &ms, &kused);
     if (st != GN_OK) return st;
@@ -488,6 +532,7 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
   if (di.status & DEV_TIMEOUT)
     return fail(GN_ERR_TIMEOUT, "gn_run: a grid-barrier wait hit its limit; the run was abandoned");
   g->has_state = true;
+  g->state_cta = kused == GN_KERNEL_CTA;
 
   gn_status result;
   if (di.iters == 0) {

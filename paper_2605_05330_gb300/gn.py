@@ -254,7 +254,7 @@ INSTANCE_CSR, INSTANCE_ASSIGNMENT = 0, 1
 class BatchInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("converged", ctypes.c_int),
                 ("binary", ctypes.c_int), ("resid_inf", ctypes.c_double), ("objective", ctypes.c_double),
-                ("safe_div_hits", ctypes.c_longlong)]
+                ("safe_div_hits", ctypes.c_longlong), ("resid_l1", ctypes.c_double), ("energy", ctypes.c_double)]
 
 
 def _batch_lib():

@@ -289,3 +289,48 @@ def test_edge_cases(gn, case, gather):
     st, mask, members, cnt, W = g.extract_is()
     np.testing.assert_array_equal(mask, oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)[1])
     assert st == "OK"
+
+
+@pytest.mark.parametrize("which", ["er2000", "udg5k_rcm", "star5000"])
+def test_cta_kernel_matches_oracle(gn, which):
+    """GN_KERNEL_CTA, the whole run in one CTA (no grid barrier): iterates against the oracle,
+    the run to a binary state against the oracle's (set, iterations on tie-free instances, the
+    report's objective, residual and energy against the persistent kernel's), and the runs it
+    refuses (start_iter > 0, resume)."""
+    if which == "er2000":
+        inst, reorder = inputs.er_graph(2000, 10.0, 1401), 0
+    elif which == "udg5k_rcm":
+        inst, reorder = inputs.unit_disk_graph(5000, 25000, 1402), 1
+    else:
+        inst, reorder = inputs.small_graph("S", 5001, [(0, i) for i in range(1, 5001)],
+                                           w=np.random.default_rng(1403).uniform(1, 100, 5001)), 0
+    g = dev_graph(gn, inst, reorder=reorder)
+    run_kw, pk = fixed_steps(20)
+    x, info = g.run(params=gn.default_params(kernel=gn.KERNEL_CTA, **pk), **run_kw)
+    assert info["kernel"] == gn.KERNEL_CTA and info["iters"] == 20
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, p=oracle.params(**pk), **run_kw)
+    assert_close_rel(to_np(x), xo)
+    p = dict(check_every=10)
+    xc, ic = g.run(max_iters=2000, tol=1e-7, params=gn.default_params(kernel=gn.KERNEL_CTA, **p))
+    st, mask, members, cnt, W = g.extract_is()
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=2000, tol=1e-7, p=oracle.params(**p))
+    assert ic["status"] == io["status"] == "OK"
+    sto, masko, memo, Wo = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, to_np(xc))
+    assert st == sto
+    np.testing.assert_array_equal(to_np(mask), masko)
+    if _tie_free(inst, oracle.params(**p)):
+        np.testing.assert_array_equal(to_np(mask), oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)[1])
+        assert ic["iters"] == io["iters"]
+    xp, ip = g.run(max_iters=2000, tol=1e-7, params=gn.default_params(**p))  # the persistent kernel
+    assert ip["kernel"] == gn.KERNEL_PERSISTENT
+    if ic["iters"] == ip["iters"]:
+        assert abs(ic["objective"] - ip["objective"]) <= 1e-6 * abs(ip["objective"])
+        assert abs(ic["resid_l1"] - ip["resid_l1"]) <= 1e-3 * max(abs(ip["resid_l1"]), 1e-12)
+        assert abs(ic["energy"] - ip["energy"]) <= 1e-5 * abs(ip["energy"])
+    with pytest.raises(gn.GNError) as e:
+        g.run(max_iters=10, start_iter=5, params=gn.default_params(kernel=gn.KERNEL_CTA))
+    assert e.value.status == "ERR_ARG"
+    g.run(max_iters=10, params=gn.default_params(kernel=gn.KERNEL_CTA))
+    with pytest.raises(gn.GNError) as e:
+        g.run(max_iters=20, start_iter=10, params=gn.default_params(resume=1))
+    assert e.value.status == "ERR_ARG"
