@@ -169,6 +169,26 @@ int32_t gn_num_vertices(const gn_graph* g);
 int64_t gn_num_entries(const gn_graph* g);
 
 /*
+ * gn_vertex_order -- the handle's internal vertex order: order[r] = the caller's id of internal
+ * vertex r (the identity for GN_REORDER_NONE).  GN_REORDER_RCM is the reverse Cuthill-McKee
+ * order: each component is searched breadth-first from its unplaced vertex of least degree
+ * (ties by id), the unplaced neighbours of each vertex follow in increasing degree (ties in
+ * adjacency order), and the whole sequence is reversed.  GN_REORDER_DEGREE is descending degree,
+ * ties by id.  Internal only: no output of the library depends on it beyond rounding order.
+ *   order  int32[n] HOST buffer, written whatever the handle's I/O mode
+ * Errors: GN_ERR_ARG (NULL handle or buffer), GN_ERR_CUDA.
+ */
+gn_status gn_vertex_order(const gn_graph* g, int32_t* order);
+
+#define GN_ORDER_FROM_HOST 1    /* the order was computed on the host */
+#define GN_ORDER_FROM_DEVICE 2  /* by the single-CTA breadth-first search on the device (RCM on
+                                   graphs of >= 16,384 vertices and degrees <= 64 whose levels fit
+                                   its shared-memory buffers; the same order as the host's) */
+/* Where the handle's internal order was computed: GN_ORDER_FROM_*, 0 without reordering or for
+ * NULL. */
+int gn_vertex_order_source(const gn_graph* g);
+
+/*
  * gn_run -- a2..a7 of the path: iterated WRGN (Def. WRGN, Def. IGN) with the gamma
  * schedule of Sec. 6, from x0, until the stop test fires or the iteration index reaches
  * max_iters; then x_out = clamp(x, 0, 1) (appendix module).

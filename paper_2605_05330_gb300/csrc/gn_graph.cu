@@ -6,10 +6,14 @@
 #include <atomic>
 #include <climits>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
+
+#include <unistd.h>
 
 #include "gn_internal.cuh"
 
@@ -130,8 +134,79 @@ gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes) {
 // neighbours by a stable insertion sort on degree.  key[v] holds the degree with the sign bit
 // set once v is placed, so each neighbour costs one random access (the traversal is bound by
 // those on graphs with random labels).
-static void rcm_order(int n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
-                      std::vector<int32_t>& perm) {
+// ---- the host worker pool behind parallel_for
+//
+// Workers start on the first multi-block job and stay, parked on a condition variable, for the
+// life of the process (a forked child starts its own set).  Jobs run one at a time; a job posted
+// from inside a job runs its blocks inline.
+namespace {
+struct HostPool {
+  std::mutex mu;
+  std::condition_variable go, done;
+  const std::function<void(int)>* job = nullptr;
+  unsigned long long gen = 0;
+  int parts = 0;
+  int pending = 0;   // workers yet to finish the current generation
+  int workers = 0;
+  pid_t pid = 0;
+};
+std::mutex g_pool_job;           // one job at a time
+HostPool* g_pool = nullptr;      // never freed: its detached workers outlive every handle
+thread_local bool t_pool_worker = false;
+
+void pool_worker(HostPool* P, int id) {
+  t_pool_worker = true;
+  unsigned long long seen = 0;
+  std::unique_lock<std::mutex> lk(P->mu);
+  for (;;) {
+    P->go.wait(lk, [&] { return P->gen != seen; });
+    seen = P->gen;
+    if (id < P->parts) {
+      const std::function<void(int)>* f = P->job;
+      lk.unlock();
+      (*f)(id);
+      lk.lock();
+    }
+    if (--P->pending == 0) P->done.notify_all();
+  }
+}
+}  // namespace
+
+void run_parts(int parts, const std::function<void(int)>& f) {
+  if (parts <= 1 || t_pool_worker) {
+    for (int t = 0; t < parts; ++t) f(t);
+    return;
+  }
+  std::lock_guard<std::mutex> job_lock(g_pool_job);
+  if (!g_pool || g_pool->pid != getpid()) {
+    HostPool* P = new HostPool();
+    P->pid = getpid();
+    P->workers = host_threads() - 1;
+    for (int i = 1; i <= P->workers; ++i) std::thread(pool_worker, P, i).detach();
+    g_pool = P;
+  }
+  HostPool* P = g_pool;
+  if (parts > P->workers + 1) {  // not reached through parallel_for
+    for (int t = 0; t < parts; ++t) f(t);
+    return;
+  }
+  {
+    std::lock_guard<std::mutex> lk(P->mu);
+    P->job = &f;
+    P->parts = parts;
+    P->pending = P->workers;
+    ++P->gen;
+  }
+  P->go.notify_all();
+  t_pool_worker = true;  // a job posted from block 0 runs inline too
+  f(0);
+  t_pool_worker = false;
+  std::unique_lock<std::mutex> lk(P->mu);
+  P->done.wait(lk, [&] { return P->pending == 0; });
+  P->job = nullptr;
+}
+
+static void rcm_order(int n, const std::vector<int32_t>& rp, const int32_t* ci, std::vector<int32_t>& perm) {
   perm.clear();
   perm.reserve(n);
   std::vector<int32_t> key(n);
@@ -198,6 +273,20 @@ extern "C" const char* gn_last_error(void) { return gn::t_last_error.c_str(); }
 
 extern "C" int32_t gn_num_vertices(const gn_graph* g) { return g ? g->n : 0; }
 extern "C" int64_t gn_num_entries(const gn_graph* g) { return g ? g->nnz : 0; }
+
+extern "C" int gn_vertex_order_source(const gn_graph* g) { return g ? g->reorder_where : 0; }
+
+extern "C" gn_status gn_vertex_order(const gn_graph* g, int32_t* order) {
+  if (!g || (!order && g->n > 0)) return gn::fail(GN_ERR_ARG, "gn_vertex_order: bad argument");
+  if (g->n == 0) return GN_OK;
+  if (!g->d_perm) {
+    for (int32_t i = 0; i < g->n; ++i) order[i] = i;
+    return GN_OK;
+  }
+  GN_CUDA(cudaMemcpyAsync(order, g->d_perm, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  return GN_OK;
+}
 
 extern "C" gn_status gn_set_io(gn_graph* g, int mem) {
   if (!g || (mem != GN_HOST && mem != GN_DEVICE)) return gn::fail(GN_ERR_ARG, "gn_set_io: bad argument");
@@ -365,10 +454,14 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
   // optional locality reordering (internal; undone on every output)
   if (reorder != GN_REORDER_NONE && n > 1) {
     std::vector<int32_t> perm;
-    std::vector<int32_t> ci_src(ci_h, ci_h + g->nnz);
     if (reorder == GN_REORDER_RCM) {
-      rcm_order(n, rp, ci_src, perm);
+      bool done = false;
+      gn_status st = rcm_order_device(g, rp, perm, &done);
+      if (st != GN_OK) return st;
+      if (!done) rcm_order(n, rp, ci_h, perm);
+      g->reorder_where = done ? GN_ORDER_FROM_DEVICE : GN_ORDER_FROM_HOST;
     } else {
+      g->reorder_where = GN_ORDER_FROM_HOST;
       perm.resize(n);
       std::iota(perm.begin(), perm.end(), 0);
       std::stable_sort(perm.begin(), perm.end(),
@@ -384,7 +477,7 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
         const int o = perm[r];
         int32_t* dst = ci2.data() + rp2[r];
         const int d = rp[o + 1] - rp[o];
-        for (int k = 0; k < d; ++k) dst[k] = iperm[ci_src[rp[o] + k]];
+        for (int k = 0; k < d; ++k) dst[k] = iperm[ci_h[rp[o] + k]];
         std::sort(dst, dst + d);
       }
     });

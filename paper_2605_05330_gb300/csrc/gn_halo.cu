@@ -45,6 +45,7 @@
 // after it has seen that they completed it.
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <vector>
 
@@ -441,25 +442,78 @@ static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 // colour c free at b; if a is also free at b use it, else swap a and c along the path from b
 // whose edges alternate a, c, a, ... -- that frees a at b and cannot reach l, which has no
 // a-edge.  lid[l] lists lane l's ids; the result col[l][k] is the column of lid[l][k].
-static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int>* col,
-                        std::vector<int>& at_l, std::vector<int>& at_b, std::vector<int>& elane,
-                        std::vector<int>& ebank, std::vector<int>& ecol, std::vector<int>& path) {
-  at_l.assign(32 * (size_t)W, -1);
-  at_b.assign(32 * (size_t)W, -1);
-  elane.clear();
-  ebank.clear();
-  ecol.clear();
+struct ColorScratch {
+  std::vector<int> at_l, at_b;           // [vertex * W + colour] -> edge, or -1 (built on demand)
+  std::vector<uint64_t> used_l, used_b;  // the colours in use as bit sets: [vertex * nw + colour / 64]
+  std::vector<int> elane, ebank, ecol, path;
+};
+
+// Most edges find a colour free at both ends; the edge tables the alternating paths walk are
+// built only when the first edge of a slice does not.
+static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int>* col, ColorScratch& cs) {
+  const int nw = (W + 63) >> 6;
+  int E = 0;
+  for (int l = 0; l < 32; ++l) E += (int)lid[l].size();
+  std::vector<int>& at_l = cs.at_l;
+  std::vector<int>& at_b = cs.at_b;
+  std::vector<uint64_t>& ul = cs.used_l;
+  std::vector<uint64_t>& ub = cs.used_b;
+  int* elane = (cs.elane.resize(E), cs.elane.data());
+  int* ebank = (cs.ebank.resize(E), cs.ebank.data());
+  int* ecol = (cs.ecol.resize(E), cs.ecol.data());
+  ul.assign(32 * (size_t)nw, 0);
+  ub.assign(32 * (size_t)nw, 0);
+  bool tables = false;
+  // the lowest colour free at a vertex (one exists below W: its edges so far are fewer than W)
+  auto lowest_free = [nw](const uint64_t* u) {
+    int w = 0;
+    while (w + 1 < nw && ~u[w] == 0) ++w;
+    return w * 64 + __builtin_ctzll(~u[w]);
+  };
+  auto put = [&](int f, int x) {  // edge f takes colour x
+    ecol[f] = x;
+    ul[elane[f] * nw + (x >> 6)] |= 1ull << (x & 63);
+    ub[ebank[f] * nw + (x >> 6)] |= 1ull << (x & 63);
+    if (tables) {
+      at_l[elane[f] * W + x] = f;
+      at_b[ebank[f] * W + x] = f;
+    }
+  };
+  auto take = [&](int f) {  // edge f gives up its colour (the tables are built)
+    const int x = ecol[f];
+    at_l[elane[f] * W + x] = -1;
+    at_b[ebank[f] * W + x] = -1;
+    ul[elane[f] * nw + (x >> 6)] &= ~(1ull << (x & 63));
+    ub[ebank[f] * nw + (x >> 6)] &= ~(1ull << (x & 63));
+  };
+  int e = 0;
   for (int l = 0; l < 32; ++l) {
-    for (size_t k = 0; k < lid[l].size(); ++k) {
-      const int e = (int)elane.size(), b = lid[l][k] & 31;
-      elane.push_back(l);
-      ebank.push_back(b);
-      ecol.push_back(-1);
-      int a = 0, c = 0;
-      while (at_l[l * W + a] >= 0) ++a;
-      while (at_b[b * W + c] >= 0) ++c;
-      if (at_b[b * W + a] >= 0) {
-        // the a/c path from bank b
+    for (size_t k = 0; k < lid[l].size(); ++k, ++e) {
+      const int b = lid[l][k] & 31;
+      elane[e] = l;
+      ebank[e] = b;
+      ecol[e] = -1;
+      // the lowest colour free at both ends when there is one below W
+      int a = -1;
+      for (int w = 0; w < nw && a < 0; ++w) {
+        const uint64_t both = ~(ul[(size_t)l * nw + w] | ub[(size_t)b * nw + w]);
+        if (both) a = w * 64 + __builtin_ctzll(both);
+      }
+      if (a >= W) a = -1;
+      if (a < 0) {
+        // a free at l, c free at b: swap a and c along the a/c path from b
+        if (!tables) {
+          at_l.assign(32 * (size_t)W, -1);
+          at_b.assign(32 * (size_t)W, -1);
+          for (int f = 0; f < e; ++f) {
+            at_l[elane[f] * W + ecol[f]] = f;
+            at_b[ebank[f] * W + ecol[f]] = f;
+          }
+          tables = true;
+        }
+        a = lowest_free(&ul[(size_t)l * nw]);
+        const int c = lowest_free(&ub[(size_t)b * nw]);
+        std::vector<int>& path = cs.path;
         path.clear();
         int v = b, cur = a;
         bool bank_side = true;
@@ -471,22 +525,13 @@ static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int
           bank_side = !bank_side;
           cur = cur == a ? c : a;
         }
-        for (int f : path) {
-          at_l[elane[f] * W + ecol[f]] = -1;
-          at_b[ebank[f] * W + ecol[f]] = -1;
-        }
-        for (int f : path) {
-          ecol[f] = ecol[f] == a ? c : a;
-          at_l[elane[f] * W + ecol[f]] = f;
-          at_b[ebank[f] * W + ecol[f]] = f;
-        }
+        for (int f : path) take(f);
+        for (int f : path) put(f, ecol[f] == a ? c : a);
       }
-      ecol[e] = a;
-      at_l[l * W + a] = e;
-      at_b[b * W + a] = e;
+      put(e, a);
     }
   }
-  int e = 0;
+  e = 0;
   for (int l = 0; l < 32; ++l) {
     col[l].resize(lid[l].size());
     for (size_t k = 0; k < lid[l].size(); ++k) col[l][k] = ecol[e++];
@@ -501,7 +546,7 @@ static constexpr double kPullDensity = 4.0;
 // the halo density; GN_GATHER_HALO_PULL / _PUSH: that one).  Sets *fits = false (and builds
 // nothing on the device) when a CTA's working set does not fit shared memory or 16-bit local
 // ids; with the automatic choice the other exchange is tried before giving up.  The per-CTA
-// work runs on the host threads (parallel_for); every CTA's output is its own.
+// work runs on the host threads, a CTA at a time (parallel_items); every CTA's output is its own.
 static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
                                    const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
                                    const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits);
@@ -517,9 +562,11 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   // 32-byte sectors of the state vector they touch
   std::vector<std::vector<int32_t>> ext(nb);
   std::vector<int64_t> sectors_of(nb, 0);
-  parallel_for(nb, 1, [&](int lo, int hi, int) {
-    std::vector<uint64_t> bits((size_t)n / 64 + 1, 0);
-    for (int b = lo; b < hi; ++b) {
+  std::vector<std::vector<uint64_t>> bitmaps(host_threads());  // per host thread, kept all-zero
+  parallel_items(nb, [&](int b, int t) {
+    std::vector<uint64_t>& bits = bitmaps[t];
+    if (bits.empty()) bits.assign((size_t)n / 64 + 1, 0);
+    {
       const int rb = part[b], re = part[b + 1];
       int wlo = INT32_MAX, whi = -1;
       for (int64_t e = rp[rb]; e < rp[re]; ++e) {
@@ -584,8 +631,8 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   // o are one run, found by binary search.
   std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
   if (push) {
-    parallel_for(nb, 1, [&](int lo, int hi, int) {
-      for (int o = lo; o < hi; ++o) {
+    parallel_items(nb, [&](int o, int) {
+      {
         for (int c = 0; c < nb; ++c) {
           const std::vector<int32_t>& xc = ext[c];
           const size_t t0 = std::lower_bound(xc.begin(), xc.end(), part[o]) - xc.begin();
@@ -600,8 +647,8 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   // pass 1, per CTA: rows into interior / boundary / heavy, slices, chunks, send pieces and
   // the block layout
   std::vector<std::vector<unsigned char>> blocks(nb);
-  parallel_for(nb, 1, [&](int lo, int hi, int) {
-    for (int b = lo; b < hi; ++b) {
+  parallel_items(nb, [&](int b, int) {
+    {
       const int rb = part[b], re = part[b + 1], nr = re - rb;
       const std::vector<int32_t>& xb = ext[b];
       // the CTAs owning the halo (xb is sorted, the partition is contiguous)
@@ -739,13 +786,25 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
 
   // pass 2, per CTA: the 16-bit local ids (own row r -> r, external halo t -> R + t,
   // padding -> the zero slot)
-  parallel_for(nb, 1, [&](int lo, int hi, int) {
-    std::vector<int32_t> extpos(std::max(n, 1), 0);
+  struct EncodeScratch {
+    std::unique_ptr<int32_t[]> extpos;  // halo slot of each external id (set before it is read)
     std::vector<uint16_t> lids[32];
     std::vector<int> cols[32];
-    std::vector<int> at_l, at_b, elane, ebank, ecol, path, occ;
+    ColorScratch cs;
+    std::vector<int> occ;
     std::vector<uint16_t> bucket[32];
-    for (int b = lo; b < hi; ++b) {
+  };
+  std::vector<EncodeScratch> scratch(host_threads());
+  parallel_items(nb, [&](int b, int t) {
+    EncodeScratch& X = scratch[t];
+    if (!X.extpos) X.extpos.reset(new int32_t[std::max(n, 1)]);
+    int32_t* extpos = X.extpos.get();
+    std::vector<uint16_t>* lids = X.lids;
+    std::vector<int>* cols = X.cols;
+    ColorScratch& cs = X.cs;
+    std::vector<int>& occ = X.occ;
+    std::vector<uint16_t>* bucket = X.bucket;
+    {
       const int rb = part[b], re = part[b + 1];
       std::vector<unsigned char>& B = blocks[b];
       HaloHeader* H = reinterpret_cast<HaloHeader*>(B.data());
@@ -776,7 +835,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
         for (int l = 0; l < 32; ++l)
           for (uint16_t id : lids[l]) ++load[id & 31];
         for (int t = 0; t < 32; ++t) Wc = std::max(Wc, load[t]);
-        color_slice(Wc, lids, cols, at_l, at_b, elane, ebank, ecol, path);
+        color_slice(Wc, lids, cols, cs);
         occ.assign(32 * (size_t)W, 0);  // occ[bank * W + column]
         for (int l = 0; l < 32; ++l)
           for (size_t t = 0; t < lids[l].size(); ++t)

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
+#include <functional>
 #include <string>
 #include <thread>
 #include <vector>
@@ -83,6 +85,7 @@ struct gn_graph {
   int32_t n = 0;
   int64_t nnz = 0;
   int reorder = GN_REORDER_NONE;
+  int reorder_where = 0;         // GN_ORDER_FROM_HOST / _DEVICE, 0 without reordering
 
   // graph (internal vertex order)
   int32_t* d_row_ptr = nullptr;
@@ -157,6 +160,9 @@ double host_gamma(const gn_params& p, int k);
 // implemented in gn_extract.cu
 gn_status state_stats(gn_graph* g, const float* x_int, double theta, double* obj, unsigned* nonbin);
 gn_status to_internal(gn_graph* g, const float* x_caller, const float** x_int);
+// implemented in gn_reorder.cu
+gn_status rcm_order_device(gn_graph* g, const std::vector<int32_t>& rp, std::vector<int32_t>& perm,
+                           bool* done);
 // implemented in gn_graph.cu
 gn_status upload_or_alias(gn_graph* g, const void* src, size_t bytes, const void** dev_ptr);
 gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes);
@@ -164,11 +170,14 @@ gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes);
 // Host-side preparation work over [0, n) split into contiguous blocks, one per host thread
 // (at most the hardware's count, and one per `grain` items): body(lo, hi, thread).  The
 // blocks are fixed by n and the thread count only, and every caller writes disjoint outputs,
-// so results do not depend on scheduling.
+// so results do not depend on scheduling.  The blocks run on a pool of worker threads started
+// once per process (run_parts, gn_graph.cu): a block costs a wake-up, not a thread start.
 inline int host_threads() {
   const unsigned h = std::thread::hardware_concurrency();
   return (int)std::max(1u, std::min(h == 0 ? 1u : h, 64u));
 }
+// runs f(0) .. f(parts - 1), parts <= host_threads(), concurrently; returns when all are done
+void run_parts(int parts, const std::function<void(int)>& f);
 template <class F>
 void parallel_for(int n, int grain, F&& body) {
   const int nt = std::max(1, std::min(host_threads(), (n + std::max(grain, 1) - 1) / std::max(grain, 1)));
@@ -176,14 +185,24 @@ void parallel_for(int n, int grain, F&& body) {
     if (n > 0) body(0, n, 0);
     return;
   }
-  std::vector<std::thread> pool;
-  pool.reserve(nt - 1);
-  for (int t = 1; t < nt; ++t) {
-    const int lo = (int)((int64_t)n * t / nt), hi = (int)((int64_t)n * (t + 1) / nt);
-    pool.emplace_back([&body, lo, hi, t] { body(lo, hi, t); });
+  run_parts(nt, [&body, n, nt](int t) {
+    body((int)((int64_t)n * t / nt), (int)((int64_t)n * (t + 1) / nt), t);
+  });
+}
+// Items [0, n) of uneven cost, handed to the host threads one at a time: body(item, thread).
+// Every item's output is its own; `thread` (< host_threads()) only selects scratch space.
+template <class F>
+void parallel_items(int n, F&& body) {
+  const int nt = std::max(1, std::min(host_threads(), n));
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) body(i, 0);
+    return;
   }
-  body(0, (int)((int64_t)n / nt), 0);
-  for (std::thread& th : pool) th.join();
+  std::atomic<int> next{0};
+  run_parts(nt, [&body, &next, n](int t) {
+    for (int i = next.fetch_add(1, std::memory_order_relaxed); i < n; i = next.fetch_add(1, std::memory_order_relaxed))
+      body(i, t);
+  });
 }
 
 }  // namespace gn

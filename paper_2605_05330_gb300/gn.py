@@ -98,6 +98,10 @@ def lib():
         L.gn_num_vertices.restype = ctypes.c_int32
         L.gn_num_entries.argtypes = [P]
         L.gn_num_entries.restype = ctypes.c_int64
+        L.gn_vertex_order.argtypes = [P, P]
+        L.gn_vertex_order.restype = ctypes.c_int
+        L.gn_vertex_order_source.argtypes = [P]
+        L.gn_vertex_order_source.restype = ctypes.c_int
         L.gn_run.argtypes = [P, P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(Params), ctypes.c_int, P,
                              ctypes.POINTER(RunInfo)]
         L.gn_run.restype = ctypes.c_int
@@ -184,6 +188,16 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+    def vertex_order(self) -> np.ndarray:
+        """The internal vertex order: entry r is the caller's id of internal vertex r."""
+        order = np.empty(max(self.n, 1), dtype=np.int32)
+        _check(lib().gn_vertex_order(self._h, order.ctypes.data_as(P)))
+        return order[: self.n]
+
+    def vertex_order_source(self) -> str:
+        """Where the internal order was computed: "host", "device", or "none" (no reordering)."""
+        return {0: "none", 1: "host", 2: "device"}[int(lib().gn_vertex_order_source(self._h))]
 
     def set_io(self, device: bool):
         _check(lib().gn_set_io(self._h, DEVICE if device else HOST))
