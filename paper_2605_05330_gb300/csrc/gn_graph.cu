@@ -9,6 +9,7 @@
 #include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -451,6 +452,8 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
     ci_h = ci_host.data();
   }
 
+  std::unique_ptr<int32_t[]> ci_renumbered;  // the rows in the internal order, when reordered
+
   // optional locality reordering (internal; undone on every output)
   if (reorder != GN_REORDER_NONE && n > 1) {
     std::vector<int32_t> perm;
@@ -467,20 +470,44 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
       std::stable_sort(perm.begin(), perm.end(),
                        [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
     }
-    std::vector<int32_t> iperm(n), rp2(n + 1), ci2((size_t)std::max<int64_t>(g->nnz, 1));
-    for (int r = 0; r < n; ++r) iperm[perm[r]] = r;
-    rp2[0] = 0;
-    for (int r = 0; r < n; ++r) rp2[r + 1] = rp2[r] + (rp[perm[r] + 1] - rp[perm[r]]);
-    // rows are independent: renumber and sort each on the host threads
-    parallel_for(n, 4096, [&](int lo, int hi, int) {
+    // iperm, the new row pointers and the renumbered rows, in two passes over row blocks on the
+    // host threads (the blocks are the same in both passes): the first scatters iperm and sums
+    // each block's degrees, the second writes each block's rows from its offset, sorted
+    std::vector<int32_t> iperm(n), rp2(n + 1);
+    std::unique_ptr<int32_t[]> ci2(new int32_t[(size_t)std::max<int64_t>(g->nnz, 1)]);
+    std::vector<int64_t> boff(host_threads() + 1, 0);
+    constexpr int kRowGrain = 4096;
+    parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
+      int64_t sum = 0;
       for (int r = lo; r < hi; ++r) {
         const int o = perm[r];
-        int32_t* dst = ci2.data() + rp2[r];
-        const int d = rp[o + 1] - rp[o];
+        iperm[o] = r;
+        sum += rp[o + 1] - rp[o];
+      }
+      boff[t + 1] = sum;
+    });
+    for (size_t t = 1; t < boff.size(); ++t) boff[t] += boff[t - 1];
+    parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
+      int32_t at = (int32_t)boff[t];
+      for (int r = lo; r < hi; ++r) {
+        const int o = perm[r], d = rp[o + 1] - rp[o];
+        rp2[r] = at;
+        int32_t* dst = ci2.get() + at;
         for (int k = 0; k < d; ++k) dst[k] = iperm[ci_h[rp[o] + k]];
-        std::sort(dst, dst + d);
+        if (d <= 32) {  // insertion sort: rows are short
+          for (int k = 1; k < d; ++k) {
+            const int32_t x = dst[k];
+            int j = k;
+            for (; j > 0 && dst[j - 1] > x; --j) dst[j] = dst[j - 1];
+            dst[j] = x;
+          }
+        } else {
+          std::sort(dst, dst + d);
+        }
+        at += d;
       }
     });
+    rp2[n] = (int32_t)g->nnz;
     float* d_w2 = nullptr;
     GN_CUDA(cudaMalloc(&g->d_perm, sizeof(int32_t) * n));
     GN_CUDA(cudaMalloc(&g->d_iperm, sizeof(int32_t) * n));
@@ -490,7 +517,7 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
     GN_CUDA(cudaMemcpyAsync(g->d_row_ptr, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                             g->stream));
     if (g->nnz > 0)
-      GN_CUDA(cudaMemcpyAsync(g->d_col_idx, ci2.data(), sizeof(int32_t) * g->nnz, cudaMemcpyHostToDevice,
+      GN_CUDA(cudaMemcpyAsync(g->d_col_idx, ci2.get(), sizeof(int32_t) * g->nnz, cudaMemcpyHostToDevice,
                               g->stream));
     k_permute_w<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_perm, g->d_w, d_w2);
     GN_LAUNCHED();
@@ -502,8 +529,8 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
     GN_LAUNCHED();
     GN_CUDA(cudaGetLastError());
     rp.swap(rp2);
-    ci_host.swap(ci2);
-    ci_h = ci_host.data();
+    ci_renumbered = std::move(ci2);
+    ci_h = ci_renumbered.get();
   }
 
   g->gather = gather;
