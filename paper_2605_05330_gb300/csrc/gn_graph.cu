@@ -309,11 +309,12 @@ extern "C" void gn_destroy(gn_graph* g) {
                    g->d_y[0], g->d_y[1], g->d_x, g->d_tmp, g->d_bsum, g->d_io, g->d_partials, g->d_bar, g->d_iterflag, g->d_inbox, g->d_info,
                    g->d_flags, g->d_red, g->d_mask, g->d_mask_c, g->d_bcount, g->d_bws,
                    g->d_members, g->d_hoff, g->d_hblob, g->d_gtab, g->d_cta_off};
-  for (void* p : dptrs)
-    if (p) cudaFree(p);
-  if (g->h_info) cudaFreeHost(g->h_info);
-  if (g->h_flags) cudaFreeHost(g->h_flags);
-  if (g->h_red) cudaFreeHost(g->h_red);
+  for (void* p : dptrs) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    if (p && !(g->d_arena && c >= g->d_arena && c < g->d_arena + g->arena_bytes)) cudaFree(p);
+  }
+  if (g->d_arena) cudaFree(g->d_arena);
+  if (g->h_arena) cudaFreeHost(g->h_arena);
   if (g->ev0) cudaEventDestroy(g->ev0);
   if (g->ev1) cudaEventDestroy(g->ev1);
   delete g;
@@ -380,31 +381,62 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
   g->nnz = rp[n];
   if (g->nnz > 0 && !col_idx) return fail(GN_ERR_ARG, "gn_create: col_idx is NULL");
 
-  size_t nb = sizeof(float) * std::max<int64_t>(n, 1);
-  GN_CUDA(cudaMalloc(&g->d_row_ptr, sizeof(int32_t) * (n + 1)));
-  GN_CUDA(cudaMalloc(&g->d_col_idx, sizeof(int32_t) * std::max<int64_t>(g->nnz, 1)));
-  GN_CUDA(cudaMalloc(&g->d_w, nb));
-  GN_CUDA(cudaMalloc(&g->d_v, nb));
-  GN_CUDA(cudaMalloc(&g->d_vlo, nb));
-  GN_CUDA(cudaMalloc(&g->d_ylo, nb));
-  GN_CUDA(cudaMalloc(&g->d_y[0], nb));
-  GN_CUDA(cudaMalloc(&g->d_y[1], nb));
-  GN_CUDA(cudaMalloc(&g->d_x, nb));
-  GN_CUDA(cudaMalloc(&g->d_tmp, nb));
-  GN_CUDA(cudaMalloc(&g->d_bsum, sizeof(double) * 4 * 1024));
-  GN_CUDA(cudaMalloc(&g->d_io, std::max<size_t>(nb, 8 * ((size_t)n + 8))));
-  GN_CUDA(cudaMalloc(&g->d_flags, sizeof(int) * 8));
-  GN_CUDA(cudaMalloc(&g->d_info, sizeof(DevInfo)));
-  GN_CUDA(cudaMalloc(&g->d_red, sizeof(double) * 8));
-  GN_CUDA(cudaMalloc(&g->d_bar, sizeof(unsigned) * 8));
-  GN_CUDA(cudaMalloc(&g->d_mask, std::max<int64_t>(n, 1)));
-  GN_CUDA(cudaMalloc(&g->d_mask_c, std::max<int64_t>(n, 1)));
-  GN_CUDA(cudaMalloc(&g->d_bcount, sizeof(int) * ((size_t)n / 256 + 2)));
-  GN_CUDA(cudaMalloc(&g->d_bws, sizeof(double) * ((size_t)n / 256 + 2)));
-  GN_CUDA(cudaMalloc(&g->d_members, sizeof(int32_t) * (std::max<int64_t>(n, 1) + 1)));
-  GN_CUDA(cudaMallocHost(&g->h_info, sizeof(DevInfo)));
-  GN_CUDA(cudaMallocHost(&g->h_flags, sizeof(int) * 8));
-  GN_CUDA(cudaMallocHost(&g->h_red, sizeof(double) * 8));
+  // the fixed-size buffers: one device allocation cut into 256-byte-aligned ranges, and one
+  // pinned host allocation (a reordered handle also gets its permutations and the permuted
+  // weights there)
+  const size_t nb = sizeof(float) * std::max<int64_t>(n, 1);
+  const bool reordering = reorder != GN_REORDER_NONE && n > 1;
+  float* d_w_perm = nullptr;
+  {
+    struct Range {
+      void** p;
+      size_t bytes;
+    };
+    const Range ranges[] = {
+        {(void**)&g->d_row_ptr, sizeof(int32_t) * ((size_t)n + 1)},
+        {(void**)&g->d_col_idx, sizeof(int32_t) * (size_t)std::max<int64_t>(g->nnz, 1)},
+        {(void**)&g->d_w, nb},
+        {(void**)&g->d_v, nb},
+        {(void**)&g->d_vlo, nb},
+        {(void**)&g->d_ylo, nb},
+        {(void**)&g->d_y[0], nb},
+        {(void**)&g->d_y[1], nb},
+        {(void**)&g->d_x, nb},
+        {(void**)&g->d_tmp, nb},
+        {(void**)&g->d_bsum, sizeof(double) * 4 * 1024},
+        {(void**)&g->d_io, std::max<size_t>(nb, 8 * ((size_t)n + 8))},
+        {(void**)&g->d_flags, sizeof(int) * 8},
+        {(void**)&g->d_info, sizeof(DevInfo)},
+        {(void**)&g->d_red, sizeof(double) * 8},
+        {(void**)&g->d_bar, sizeof(unsigned) * 8},
+        {(void**)&g->d_mask, (size_t)std::max<int64_t>(n, 1)},
+        {(void**)&g->d_mask_c, (size_t)std::max<int64_t>(n, 1)},
+        {(void**)&g->d_bcount, sizeof(int) * ((size_t)n / 256 + 2)},
+        {(void**)&g->d_bws, sizeof(double) * ((size_t)n / 256 + 2)},
+        {(void**)&g->d_members, sizeof(int32_t) * ((size_t)std::max<int64_t>(n, 1) + 1)},
+        {reordering ? (void**)&g->d_perm : nullptr, sizeof(int32_t) * (size_t)n},
+        {reordering ? (void**)&g->d_iperm : nullptr, sizeof(int32_t) * (size_t)n},
+        {reordering ? (void**)&d_w_perm : nullptr, nb},
+    };
+    auto round256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t total = 0;
+    for (const Range& r : ranges)
+      if (r.p) total += round256(r.bytes);
+    GN_CUDA(cudaMalloc(&g->d_arena, total));
+    g->arena_bytes = total;
+    size_t at = 0;
+    for (const Range& r : ranges)
+      if (r.p) {
+        *r.p = g->d_arena + at;
+        at += round256(r.bytes);
+      }
+    const size_t h_bytes = 256 + 64 + 64;  // DevInfo, 8 flags, 8 doubles
+    static_assert(sizeof(DevInfo) <= 256, "DevInfo grew past its pinned slot");
+    GN_CUDA(cudaMallocHost(&g->h_arena, h_bytes));
+    g->h_info = reinterpret_cast<DevInfo*>(g->h_arena);
+    g->h_flags = reinterpret_cast<int*>(g->h_arena + 256);
+    g->h_red = reinterpret_cast<double*>(g->h_arena + 320);
+  }
   GN_CUDA(cudaEventCreate(&g->ev0));
   GN_CUDA(cudaEventCreate(&g->ev1));
 
@@ -508,10 +540,7 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
       }
     });
     rp2[n] = (int32_t)g->nnz;
-    float* d_w2 = nullptr;
-    GN_CUDA(cudaMalloc(&g->d_perm, sizeof(int32_t) * n));
-    GN_CUDA(cudaMalloc(&g->d_iperm, sizeof(int32_t) * n));
-    GN_CUDA(cudaMalloc(&d_w2, sizeof(float) * n));
+    float* d_w2 = d_w_perm;  // the weights in the internal order (the caller-order copy stays unused)
     GN_CUDA(cudaMemcpyAsync(g->d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
     GN_CUDA(cudaMemcpyAsync(g->d_iperm, iperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
     GN_CUDA(cudaMemcpyAsync(g->d_row_ptr, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
@@ -522,8 +551,6 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
     k_permute_w<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_perm, g->d_w, d_w2);
     GN_LAUNCHED();
     GN_CUDA(cudaGetLastError());
-    GN_CUDA(cudaStreamSynchronize(g->stream));
-    cudaFree(g->d_w);
     g->d_w = d_w2;
     k_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_w, g->d_v, g->d_vlo, g->d_flags);
     GN_LAUNCHED();

@@ -135,6 +135,11 @@ struct gn_graph {
   int* h_flags = nullptr;                  // pinned
   double* d_red = nullptr;                 // small FP64 scratch for reductions
   double* h_red = nullptr;                 // pinned
+  // gn_create's fixed-size buffers live in one device allocation and one pinned host allocation;
+  // the pointers into them are freed with them, not one by one
+  unsigned char* d_arena = nullptr;
+  size_t arena_bytes = 0;
+  unsigned char* h_arena = nullptr;
   uint8_t* d_mask = nullptr;    // rounded set, internal order
   uint8_t* d_mask_c = nullptr;  // rounded set, caller order
   int* d_bcount = nullptr;      // per-CTA member counts / offsets (extraction)
