@@ -19,6 +19,7 @@
 #include <cstring>
 #include <vector>
 
+#include "gn_internal.cuh"
 #include "gn_iter_common.cuh"
 
 namespace gn {

@@ -21,6 +21,7 @@
 #include <numeric>
 #include <vector>
 
+#include "gn_internal.cuh"
 #include "gn_iter_common.cuh"
 
 namespace gn {

@@ -1,0 +1,503 @@
+// gn_halo_build.cu -- host side of the halo gather mode: each CTA's halo list, the exchange
+// (pull or push) and the packed per-CTA blocks (gn_halo.cuh) with their SELL-32 slices, heavy
+// row chunks and send lists, uploaded once per graph.  The layout itself is described in
+// gn_halo.cu.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "gn_halo.cuh"
+#include "gn_internal.cuh"
+
+namespace gn {
+
+static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Bank-conflict-free SELL columns.  In a slice, lane l's row has its entries (local ids, bank
+// = id mod 32) and column c of the slice is one gather instruction over the 32 lanes.  The
+// entries form a bipartite multigraph lanes x banks; colouring its edges with W colours so
+// that no two edges at a lane or at a bank share a colour puts every lane's entries in
+// distinct columns and every column's entries in distinct banks.  W colours suffice when W >=
+// every lane's degree and every bank's load (Konig's edge-colouring theorem).  Alternating-path
+// method: for an edge (l, b) take a colour a free at l and a
+// colour c free at b; if a is also free at b use it, else swap a and c along the path from b
+// whose edges alternate a, c, a, ... -- that frees a at b and cannot reach l, which has no
+// a-edge.  lid[l] lists lane l's ids; the result col[l][k] is the column of lid[l][k].
+struct ColorScratch {
+  std::vector<int> at_l, at_b;           // [vertex * W + colour] -> edge, or -1 (built on demand)
+  std::vector<uint64_t> used_l, used_b;  // the colours in use as bit sets: [vertex * nw + colour / 64]
+  std::vector<int> elane, ebank, ecol, path;
+};
+
+// Most edges find a colour free at both ends; the edge tables the alternating paths walk are
+// built only when the first edge of a slice does not.
+static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int>* col, ColorScratch& cs) {
+  const int nw = (W + 63) >> 6;
+  int E = 0;
+  for (int l = 0; l < 32; ++l) E += (int)lid[l].size();
+  std::vector<int>& at_l = cs.at_l;
+  std::vector<int>& at_b = cs.at_b;
+  std::vector<uint64_t>& ul = cs.used_l;
+  std::vector<uint64_t>& ub = cs.used_b;
+  int* elane = (cs.elane.resize(E), cs.elane.data());
+  int* ebank = (cs.ebank.resize(E), cs.ebank.data());
+  int* ecol = (cs.ecol.resize(E), cs.ecol.data());
+  ul.assign(32 * (size_t)nw, 0);
+  ub.assign(32 * (size_t)nw, 0);
+  bool tables = false;
+  // the lowest colour free at a vertex (one exists below W: its edges so far are fewer than W)
+  auto lowest_free = [nw](const uint64_t* u) {
+    int w = 0;
+    while (w + 1 < nw && ~u[w] == 0) ++w;
+    return w * 64 + __builtin_ctzll(~u[w]);
+  };
+  auto put = [&](int f, int x) {  // edge f takes colour x
+    ecol[f] = x;
+    ul[elane[f] * nw + (x >> 6)] |= 1ull << (x & 63);
+    ub[ebank[f] * nw + (x >> 6)] |= 1ull << (x & 63);
+    if (tables) {
+      at_l[elane[f] * W + x] = f;
+      at_b[ebank[f] * W + x] = f;
+    }
+  };
+  auto take = [&](int f) {  // edge f gives up its colour (the tables are built)
+    const int x = ecol[f];
+    at_l[elane[f] * W + x] = -1;
+    at_b[ebank[f] * W + x] = -1;
+    ul[elane[f] * nw + (x >> 6)] &= ~(1ull << (x & 63));
+    ub[ebank[f] * nw + (x >> 6)] &= ~(1ull << (x & 63));
+  };
+  int e = 0;
+  for (int l = 0; l < 32; ++l) {
+    for (size_t k = 0; k < lid[l].size(); ++k, ++e) {
+      const int b = lid[l][k] & 31;
+      elane[e] = l;
+      ebank[e] = b;
+      ecol[e] = -1;
+      // the lowest colour free at both ends when there is one below W
+      int a = -1;
+      for (int w = 0; w < nw && a < 0; ++w) {
+        const uint64_t both = ~(ul[(size_t)l * nw + w] | ub[(size_t)b * nw + w]);
+        if (both) a = w * 64 + __builtin_ctzll(both);
+      }
+      if (a >= W) a = -1;
+      if (a < 0) {
+        // a free at l, c free at b: swap a and c along the a/c path from b
+        if (!tables) {
+          at_l.assign(32 * (size_t)W, -1);
+          at_b.assign(32 * (size_t)W, -1);
+          for (int f = 0; f < e; ++f) {
+            at_l[elane[f] * W + ecol[f]] = f;
+            at_b[ebank[f] * W + ecol[f]] = f;
+          }
+          tables = true;
+        }
+        a = lowest_free(&ul[(size_t)l * nw]);
+        const int c = lowest_free(&ub[(size_t)b * nw]);
+        std::vector<int>& path = cs.path;
+        path.clear();
+        int v = b, cur = a;
+        bool bank_side = true;
+        for (;;) {
+          const int f = bank_side ? at_b[v * W + cur] : at_l[v * W + cur];
+          if (f < 0) break;
+          path.push_back(f);
+          v = bank_side ? elane[f] : ebank[f];
+          bank_side = !bank_side;
+          cur = cur == a ? c : a;
+        }
+        for (int f : path) take(f);
+        for (int f : path) put(f, ecol[f] == a ? c : a);
+      }
+      put(e, a);
+    }
+  }
+  e = 0;
+  for (int l = 0; l < 32; ++l) {
+    col[l].resize(lid[l].size());
+    for (size_t k = 0; k < lid[l].size(); ++k) col[l][k] = ecol[e++];
+  }
+}
+
+// A CTA's halo is "dense" when it averages at least this many values per 32-byte sector:
+// then the pull exchange reads few sectors and wins; below it the push exchange does.
+static constexpr double kPullDensity = 4.0;
+
+// Builds the blocks for the partition `part`, for the exchange `want` (GN_GATHER_HALO: by
+// the halo density; GN_GATHER_HALO_PULL / _PUSH: that one).  Sets *fits = false (and builds
+// nothing on the device) when a CTA's working set does not fit shared memory or 16-bit local
+// ids; with the automatic choice the other exchange is tried before giving up.  The per-CTA
+// work runs on the host threads, a CTA at a time (parallel_items); every CTA's output is its own.
+static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
+                                   const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                                   const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits);
+
+gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
+                     const std::vector<int32_t>& part, size_t smem_limit, int want, bool* fits) {
+  *fits = false;
+  const int nb = (int)part.size() - 1;
+  const int n = g->n;
+
+  // halos: each CTA's distinct external neighbours in increasing id order, from a bitmap of
+  // the vertex range (a mark per entry, then a scan of the marked words), and the number of
+  // 32-byte sectors of the state vector they touch
+  std::vector<std::vector<int32_t>> ext(nb);
+  std::vector<int64_t> sectors_of(nb, 0);
+  std::vector<std::vector<uint64_t>> bitmaps(host_threads());  // per host thread, kept all-zero
+  parallel_items(nb, [&](int b, int t) {
+    std::vector<uint64_t>& bits = bitmaps[t];
+    if (bits.empty()) bits.assign((size_t)n / 64 + 1, 0);
+    {
+      const int rb = part[b], re = part[b + 1];
+      int wlo = INT32_MAX, whi = -1;
+      for (int64_t e = rp[rb]; e < rp[re]; ++e) {
+        const int j = ci[e];
+        if (j >= rb && j < re) continue;
+        bits[j >> 6] |= 1ull << (j & 63);
+        wlo = std::min(wlo, j >> 6);
+        whi = std::max(whi, j >> 6);
+      }
+      std::vector<int32_t>& xb = ext[b];
+      int64_t sec = 0, last = -1;
+      for (int wd = wlo; wd <= whi; ++wd) {
+        uint64_t m = bits[wd];
+        bits[wd] = 0;
+        while (m) {
+          const int j = wd * 64 + __builtin_ctzll(m);
+          m &= m - 1;
+          xb.push_back(j);
+          sec += (j / 8 != last);
+          last = j / 8;
+        }
+      }
+      sectors_of[b] = sec;
+    }
+  });
+  std::vector<int64_t> inbox_off(nb + 1, 0);
+  int64_t vals = 0, sectors = 0;
+  for (int b = 0; b < nb; ++b) {
+    inbox_off[b + 1] = inbox_off[b] + (int64_t)((ext[b].size() + 3) & ~(size_t)3);
+    vals += (int64_t)ext[b].size();
+    sectors += sectors_of[b];
+  }
+  // the exchange: forced, or by the density of the halos in memory
+  bool push = want == GN_GATHER_HALO_PUSH ||
+              (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
+  if (push && inbox_off[nb] > (int64_t)INT32_MAX) {  // inbox slots do not fit 32 bits
+    if (want == GN_GATHER_HALO_PUSH) return GN_OK;
+    push = false;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt, push = !push) {
+    if (attempt == 1 && want != GN_GATHER_HALO) break;
+    gn_status st = build_halo_blocks(g, rp, ci, part, ext, inbox_off, push, smem_limit, fits);
+    if (st != GN_OK || *fits) return st;
+  }
+  return GN_OK;
+}
+
+// The blocks for one exchange (see build_halo).
+static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
+                                   const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                                   const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits) {
+  *fits = false;
+  const int nb = (int)part.size() - 1;
+  const int n = g->n;
+  int max_rows = 0;
+  for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
+  const int R = (max_rows + 3) & ~3;
+  auto owner = [&](int j) { return (int)(std::upper_bound(part.begin(), part.end(), j) - part.begin()) - 1; };
+
+  // send lists: for each owner o, the (inbox slot, own row) pairs in slot order.  The slots of
+  // consumer c come before those of c + 1, and within c's halo (sorted by id) the vertices of
+  // o are one run, found by binary search.
+  std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
+  if (push) {
+    parallel_items(nb, [&](int o, int) {
+      {
+        for (int c = 0; c < nb; ++c) {
+          const std::vector<int32_t>& xc = ext[c];
+          const size_t t0 = std::lower_bound(xc.begin(), xc.end(), part[o]) - xc.begin();
+          const size_t t1 = std::lower_bound(xc.begin() + t0, xc.end(), part[o + 1]) - xc.begin();
+          for (size_t t = t0; t < t1; ++t)
+            sends[o].push_back({(int32_t)(inbox_off[c] + (int64_t)t), xc[t] - part[o]});
+        }
+      }
+    });
+  }
+
+  // pass 1, per CTA: rows into interior / boundary / heavy, slices, chunks, send pieces and
+  // the block layout
+  std::vector<std::vector<unsigned char>> blocks(nb);
+  parallel_items(nb, [&](int b, int) {
+    {
+      const int rb = part[b], re = part[b + 1], nr = re - rb;
+      const std::vector<int32_t>& xb = ext[b];
+      // the CTAs owning the halo (xb is sorted, the partition is contiguous)
+      std::vector<int32_t> dep;
+      for (int j : xb) {
+        const int o = owner(j);
+        if (dep.empty() || dep.back() != o) dep.push_back(o);
+      }
+      std::vector<int> light_int, light_bnd, heavy;
+      for (int r = 0; r < nr; ++r) {
+        const int64_t a = rp[rb + r], c = rp[rb + r + 1];
+        if (c - a > kHeavyHalo) {
+          heavy.push_back(r);
+          continue;
+        }
+        bool bnd = false;
+        for (int64_t e = a; e < c && !bnd; ++e) bnd = (ci[e] < rb || ci[e] >= re);
+        (bnd ? light_bnd : light_int).push_back(r);
+      }
+      auto by_deg = [&](int x, int y) {
+        const int dx = rp[rb + x + 1] - rp[rb + x], dy = rp[rb + y + 1] - rp[rb + y];
+        return dx != dy ? dx > dy : x < y;
+      };
+      std::sort(light_int.begin(), light_int.end(), by_deg);
+      std::sort(light_bnd.begin(), light_bnd.end(), by_deg);
+      // interior-only slices first; the rest (the interior tail + boundary rows) after
+      const int ns_int = (int)light_int.size() / 32;
+      std::vector<int> order(light_int.begin(), light_int.end());
+      order.insert(order.end(), light_bnd.begin(), light_bnd.end());
+      const int ns = ((int)order.size() + 31) / 32;
+      HaloHeader H;
+      memset(&H, 0, sizeof H);
+      H.ns_int = ns_int;
+      H.ns = ns;
+      H.nheavy = (int)heavy.size();
+      H.lx = (int)xb.size();
+      H.ndep = (int)dep.size();
+      H.inbox_off = (int)inbox_off[b];
+      std::vector<int2> meta(ns);
+      std::vector<short> srow((size_t)ns * 32, (short)-1);
+      int sell_len = 0;
+      // slice width: the longest row (widening to the busiest bank's load, which would make
+      // every gather conflict-free, measured slower: the extra columns cost more than the
+      // conflicts they remove)
+      for (int s = 0; s < ns; ++s) {
+        int wmax = 0;
+        for (int l = 0; l < 32; ++l) {
+          const size_t q = (size_t)s * 32 + l;
+          if (q < order.size()) {
+            const int r = order[q];
+            srow[q] = (short)r;
+            wmax = std::max(wmax, (int)(rp[rb + r + 1] - rp[rb + r]));
+          }
+        }
+        wmax = (wmax + 3) & ~3;
+        meta[s] = make_int2(sell_len, wmax);
+        sell_len += wmax * 32;
+      }
+      // heavy rows: (row, first chunk, chunks); chunks: (entry offset into hl, count)
+      int heavy_len = 0;
+      std::vector<int> hmeta, hchunk;
+      for (int r : heavy) {
+        const int d = rp[rb + r + 1] - rp[rb + r];
+        hmeta.push_back(r);
+        hmeta.push_back((int)hchunk.size() / 2);
+        hmeta.push_back((d + kHeavyChunk - 1) / kHeavyChunk);
+        for (int a = 0; a < d; a += kHeavyChunk) {
+          hchunk.push_back(heavy_len + a);
+          hchunk.push_back(std::min(kHeavyChunk, d - a));
+        }
+        heavy_len += d;
+      }
+      H.sell_len = sell_len;
+      H.heavy_len = heavy_len;
+      H.nchunk = (int)hchunk.size() / 2;
+      // send pieces: runs of consecutive inbox slots, at most kSendPiece long
+      const std::vector<std::pair<int32_t, int32_t>>& sd = sends[b];
+      std::vector<int4> pieces;
+      std::vector<uint16_t> src(sd.size());
+      for (size_t e = 0; e < sd.size(); ++e) {
+        src[e] = (uint16_t)sd[e].second;
+        if (pieces.empty() || pieces.back().y == kSendPiece || sd[e].first != pieces.back().x + pieces.back().y)
+          pieces.push_back(make_int4(sd[e].first, 0, (int)e, 0));
+        ++pieces.back().y;
+      }
+      H.npiece = (int)pieces.size();
+      size_t off = align16(sizeof(HaloHeader));
+      H.off_meta = (int)off;
+      off = align16(off + sizeof(int2) * ns);
+      H.off_srow = (int)off;
+      off = align16(off + sizeof(short) * 32 * (size_t)ns);
+      H.off_sell = (int)off;
+      off = align16(off + 2 * (size_t)sell_len);
+      H.off_hmeta = (int)off;
+      off = align16(off + 4 * hmeta.size());
+      H.off_hl = (int)off;
+      off = align16(off + 2 * (size_t)heavy_len);
+      H.off_dep = (int)off;
+      off = align16(off + 4 * dep.size());
+      H.off_hchunk = (int)off;
+      off = align16(off + 4 * hchunk.size());
+      H.off_hpart = (int)off;
+      off = align16(off + 4 * (size_t)H.nchunk);
+      H.off_piece = (int)off;
+      off = align16(off + sizeof(int4) * pieces.size());
+      H.off_src = (int)off;
+      off = align16(off + 2 * src.size());
+      H.off_x = (int)off;
+      if (!push) off = align16(off + 4 * xb.size());
+      H.bytes = (int)off;
+      std::vector<unsigned char>& B = blocks[b];
+      B.assign(off, 0);
+      memcpy(B.data(), &H, sizeof H);
+      if (ns) memcpy(B.data() + H.off_meta, meta.data(), sizeof(int2) * ns);
+      if (ns) memcpy(B.data() + H.off_srow, srow.data(), sizeof(short) * 32 * (size_t)ns);
+      if (!hmeta.empty()) memcpy(B.data() + H.off_hmeta, hmeta.data(), 4 * hmeta.size());
+      if (!dep.empty()) memcpy(B.data() + H.off_dep, dep.data(), 4 * dep.size());
+      if (!hchunk.empty()) memcpy(B.data() + H.off_hchunk, hchunk.data(), 4 * hchunk.size());
+      if (!pieces.empty()) memcpy(B.data() + H.off_piece, pieces.data(), sizeof(int4) * pieces.size());
+      if (!src.empty()) memcpy(B.data() + H.off_src, src.data(), 2 * src.size());
+      if (!push && !xb.empty()) memcpy(B.data() + H.off_x, xb.data(), 4 * xb.size());
+    }
+  });
+  int lx_max = 0;
+  size_t blk_max = 0;
+  for (int b = 0; b < nb; ++b) {
+    lx_max = std::max(lx_max, (int)ext[b].size());
+    blk_max = std::max(blk_max, blocks[b].size());
+  }
+  const int Lp = (lx_max + 3) & ~3;
+  const int zero_id = R + Lp;  // 32 zero slots from here, one per bank
+  const size_t floats = (size_t)6 * R + Lp + 32;
+  const size_t smem = 4 * floats + blk_max;
+  if (zero_id + 31 > 65535 || smem > smem_limit || R > 32767) return GN_OK;  // does not fit
+
+  // pass 2, per CTA: the 16-bit local ids (own row r -> r, external halo t -> R + t,
+  // padding -> the zero slot)
+  struct EncodeScratch {
+    std::unique_ptr<int32_t[]> extpos;  // halo slot of each external id (set before it is read)
+    std::vector<uint16_t> lids[32];
+    std::vector<int> cols[32];
+    ColorScratch cs;
+    std::vector<int> occ;
+    std::vector<uint16_t> bucket[32];
+  };
+  std::vector<EncodeScratch> scratch(host_threads());
+  parallel_items(nb, [&](int b, int t) {
+    EncodeScratch& X = scratch[t];
+    if (!X.extpos) X.extpos.reset(new int32_t[std::max(n, 1)]);
+    int32_t* extpos = X.extpos.get();
+    std::vector<uint16_t>* lids = X.lids;
+    std::vector<int>* cols = X.cols;
+    ColorScratch& cs = X.cs;
+    std::vector<int>& occ = X.occ;
+    std::vector<uint16_t>* bucket = X.bucket;
+    {
+      const int rb = part[b], re = part[b + 1];
+      std::vector<unsigned char>& B = blocks[b];
+      HaloHeader* H = reinterpret_cast<HaloHeader*>(B.data());
+      H->zero_id = zero_id;
+      for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = (int32_t)t;
+      auto lid = [&](int j) -> uint16_t {
+        return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
+      };
+      const int2* meta = reinterpret_cast<const int2*>(B.data() + H->off_meta);
+      const short* srow = reinterpret_cast<const short*>(B.data() + H->off_srow);
+      uint16_t* sell = reinterpret_cast<uint16_t*>(B.data() + H->off_sell);
+      // Every lane's row may list its entries in any order: colour the slice (color_slice) so
+      // that each column's real entries lie in distinct banks, then pad each lane's empty
+      // columns with the zero slot of a bank no real entry of that column uses (all padding of
+      // a column reads that one address: a broadcast).
+      for (int s = 0; s < H->ns; ++s) {
+        const int W = meta[s].y;
+        for (int l = 0; l < 32; ++l) {
+          const int r = srow[s * 32 + l];
+          lids[l].clear();
+          if (r >= 0)
+            for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) lids[l].push_back(lid(ci[e]));
+        }
+        // colours for the slice's busiest bank; when that is more than the slice's width, the
+        // colours past the width fold into each lane's free columns, least-used bank first
+        // (only those gathers can conflict)
+        int Wc = W, load[32] = {0};
+        for (int l = 0; l < 32; ++l)
+          for (uint16_t id : lids[l]) ++load[id & 31];
+        for (int t = 0; t < 32; ++t) Wc = std::max(Wc, load[t]);
+        color_slice(Wc, lids, cols, cs);
+        occ.assign(32 * (size_t)W, 0);  // occ[bank * W + column]
+        for (int l = 0; l < 32; ++l)
+          for (size_t t = 0; t < lids[l].size(); ++t)
+            if (cols[l][t] < W) ++occ[(lids[l][t] & 31) * W + cols[l][t]];
+        if (Wc > W) {
+          for (int l = 0; l < 32; ++l) {
+            uint64_t used = 0;
+            for (size_t t = 0; t < lids[l].size(); ++t)
+              if (cols[l][t] < W) used |= 1ull << cols[l][t];
+            for (size_t t = 0; t < lids[l].size(); ++t) {
+              if (cols[l][t] < W) continue;
+              const int bk = lids[l][t] & 31;
+              int best = -1;
+              for (int k = 0; k < W; ++k)
+                if (!(used >> k & 1ull) && (best < 0 || occ[bk * W + k] < occ[bk * W + best])) best = k;
+              cols[l][t] = best;
+              used |= 1ull << best;
+              ++occ[bk * W + best];
+            }
+          }
+        }
+        for (int k = 0; k < W; ++k) {
+          int zb = 0;  // the bank least used by column k's real entries (unused when one exists)
+          for (int t = 1; t < 32; ++t)
+            if (occ[t * W + k] < occ[zb * W + k]) zb = t;
+          const uint16_t zero = (uint16_t)(zero_id + ((zb - zero_id) & 31));
+          for (int l = 0; l < 32; ++l) sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = zero;
+        }
+        for (int l = 0; l < 32; ++l)
+          for (size_t t = 0; t < lids[l].size(); ++t) {
+            const int k = cols[l][t];
+            sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = lids[l][t];
+          }
+      }
+      const int* hm = reinterpret_cast<const int*>(B.data() + H->off_hmeta);
+      const int* hc = reinterpret_cast<const int*>(B.data() + H->off_hchunk);
+      uint16_t* hl = reinterpret_cast<uint16_t*>(B.data() + H->off_hl);
+      // heavy rows: entries dealt round-robin over the banks, so each group of 32 consecutive
+      // entries (one gather instruction of sum_chunk) spreads over the banks
+      for (int h = 0; h < H->nheavy; ++h) {
+        const int r = hm[3 * h], o = hc[2 * hm[3 * h + 1]];  // the row's entries start at its first chunk
+        const int d = rp[rb + r + 1] - rp[rb + r];
+        size_t most = 0;
+        for (int t = 0; t < 32; ++t) bucket[t].clear();
+        for (int k = 0; k < d; ++k) {
+          const uint16_t id = lid(ci[rp[rb + r] + k]);
+          bucket[id & 31].push_back(id);
+        }
+        for (int t = 0; t < 32; ++t) most = std::max(most, bucket[t].size());
+        int k = 0;
+        for (size_t j = 0; j < most; ++j)
+          for (int t = 0; t < 32; ++t)
+            if (j < bucket[t].size()) hl[o + k++] = bucket[t][j];
+      }
+    }
+  });
+  std::vector<int64_t> hoff(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) hoff[b + 1] = hoff[b] + (int64_t)blocks[b].size();
+  std::vector<unsigned char> blob((size_t)std::max<int64_t>(hoff[nb], 16));
+  parallel_for(nb, 8, [&](int lo, int hi, int) {
+    for (int b = lo; b < hi; ++b) memcpy(blob.data() + hoff[b], blocks[b].data(), blocks[b].size());
+  });
+  GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
+  GN_CUDA(cudaMalloc(&g->d_hblob, blob.size()));
+  if (push) {
+    g->inbox_len = std::max<int64_t>(inbox_off[nb], 4);
+    GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 2 * (size_t)g->inbox_len));
+    GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 2 * (size_t)g->inbox_len, g->stream));
+  }
+  g->halo_push = push;
+  GN_CUDA(cudaMemcpyAsync(g->d_hoff, hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, g->stream));
+  GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  g->halo_pad = Lp;
+  g->rows_pad_halo = R;
+  g->smem_bytes = smem;
+  *fits = true;
+  return GN_OK;
+}
+
+}  // namespace gn

@@ -3,7 +3,7 @@
 // partials, the bounded grid barrier and the stop decision.
 #pragma once
 
-#include "gn_internal.cuh"
+#include "gn_device.cuh"
 
 namespace gn {
 

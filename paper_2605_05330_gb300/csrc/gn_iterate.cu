@@ -18,6 +18,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "gn_internal.cuh"
 #include "gn_iter_common.cuh"
 
 namespace gn {
