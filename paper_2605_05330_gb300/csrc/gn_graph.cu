@@ -489,12 +489,12 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
   // optional locality reordering (internal; undone on every output)
   if (reorder != GN_REORDER_NONE && n > 1) {
     std::vector<int32_t> perm;
+    bool on_device = false;  // order and renumbering done on the device (RCM in its scope)
     if (reorder == GN_REORDER_RCM) {
-      bool done = false;
-      gn_status st = rcm_order_device(g, rp, perm, &done);
+      gn_status st = rcm_reorder_device(g, rp, ci_renumbered, &on_device);
       if (st != GN_OK) return st;
-      if (!done) rcm_order(n, rp, ci_h, perm);
-      g->reorder_where = done ? GN_ORDER_FROM_DEVICE : GN_ORDER_FROM_HOST;
+      if (!on_device) rcm_order(n, rp, ci_h, perm);
+      g->reorder_where = on_device ? GN_ORDER_FROM_DEVICE : GN_ORDER_FROM_HOST;
     } else {
       g->reorder_where = GN_ORDER_FROM_HOST;
       perm.resize(n);
@@ -502,52 +502,57 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
       std::stable_sort(perm.begin(), perm.end(),
                        [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
     }
-    // iperm, the new row pointers and the renumbered rows, in two passes over row blocks on the
-    // host threads (the blocks are the same in both passes): the first scatters iperm and sums
-    // each block's degrees, the second writes each block's rows from its offset, sorted
-    std::vector<int32_t> iperm(n), rp2(n + 1);
-    std::unique_ptr<int32_t[]> ci2(new int32_t[(size_t)std::max<int64_t>(g->nnz, 1)]);
-    std::vector<int64_t> boff(host_threads() + 1, 0);
-    constexpr int kRowGrain = 4096;
-    parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
-      int64_t sum = 0;
-      for (int r = lo; r < hi; ++r) {
-        const int o = perm[r];
-        iperm[o] = r;
-        sum += rp[o + 1] - rp[o];
-      }
-      boff[t + 1] = sum;
-    });
-    for (size_t t = 1; t < boff.size(); ++t) boff[t] += boff[t - 1];
-    parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
-      int32_t at = (int32_t)boff[t];
-      for (int r = lo; r < hi; ++r) {
-        const int o = perm[r], d = rp[o + 1] - rp[o];
-        rp2[r] = at;
-        int32_t* dst = ci2.get() + at;
-        for (int k = 0; k < d; ++k) dst[k] = iperm[ci_h[rp[o] + k]];
-        if (d <= 32) {  // insertion sort: rows are short
-          for (int k = 1; k < d; ++k) {
-            const int32_t x = dst[k];
-            int j = k;
-            for (; j > 0 && dst[j - 1] > x; --j) dst[j] = dst[j - 1];
-            dst[j] = x;
-          }
-        } else {
-          std::sort(dst, dst + d);
+    if (!on_device) {
+      // iperm, the new row pointers and the renumbered rows, in two passes over row blocks on the
+      // host threads (the blocks are the same in both passes): the first scatters iperm and sums
+      // each block's degrees, the second writes each block's rows from its offset, sorted
+      std::vector<int32_t> iperm(n), rp2(n + 1);
+      std::unique_ptr<int32_t[]> ci2(new int32_t[(size_t)std::max<int64_t>(g->nnz, 1)]);
+      std::vector<int64_t> boff(host_threads() + 1, 0);
+      constexpr int kRowGrain = 4096;
+      parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
+        int64_t sum = 0;
+        for (int r = lo; r < hi; ++r) {
+          const int o = perm[r];
+          iperm[o] = r;
+          sum += rp[o + 1] - rp[o];
         }
-        at += d;
-      }
-    });
-    rp2[n] = (int32_t)g->nnz;
-    float* d_w2 = d_w_perm;  // the weights in the internal order (the caller-order copy stays unused)
-    GN_CUDA(cudaMemcpyAsync(g->d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
-    GN_CUDA(cudaMemcpyAsync(g->d_iperm, iperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
-    GN_CUDA(cudaMemcpyAsync(g->d_row_ptr, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
-                            g->stream));
-    if (g->nnz > 0)
-      GN_CUDA(cudaMemcpyAsync(g->d_col_idx, ci2.get(), sizeof(int32_t) * g->nnz, cudaMemcpyHostToDevice,
+        boff[t + 1] = sum;
+      });
+      for (size_t t = 1; t < boff.size(); ++t) boff[t] += boff[t - 1];
+      parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
+        int32_t at = (int32_t)boff[t];
+        for (int r = lo; r < hi; ++r) {
+          const int o = perm[r], d = rp[o + 1] - rp[o];
+          rp2[r] = at;
+          int32_t* dst = ci2.get() + at;
+          for (int k = 0; k < d; ++k) dst[k] = iperm[ci_h[rp[o] + k]];
+          if (d <= 32) {  // insertion sort: rows are short
+            for (int k = 1; k < d; ++k) {
+              const int32_t x = dst[k];
+              int j = k;
+              for (; j > 0 && dst[j - 1] > x; --j) dst[j] = dst[j - 1];
+              dst[j] = x;
+            }
+          } else {
+            std::sort(dst, dst + d);
+          }
+          at += d;
+        }
+      });
+      rp2[n] = (int32_t)g->nnz;
+      GN_CUDA(cudaMemcpyAsync(g->d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
+      GN_CUDA(cudaMemcpyAsync(g->d_iperm, iperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
+      GN_CUDA(cudaMemcpyAsync(g->d_row_ptr, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                               g->stream));
+      if (g->nnz > 0)
+        GN_CUDA(cudaMemcpyAsync(g->d_col_idx, ci2.get(), sizeof(int32_t) * g->nnz, cudaMemcpyHostToDevice,
+                                g->stream));
+      rp.swap(rp2);
+      ci_renumbered = std::move(ci2);
+    }
+    ci_h = ci_renumbered.get();
+    float* d_w2 = d_w_perm;  // the weights in the internal order (the caller-order copy stays unused)
     k_permute_w<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_perm, g->d_w, d_w2);
     GN_LAUNCHED();
     GN_CUDA(cudaGetLastError());
@@ -555,9 +560,6 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
     k_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_w, g->d_v, g->d_vlo, g->d_flags);
     GN_LAUNCHED();
     GN_CUDA(cudaGetLastError());
-    rp.swap(rp2);
-    ci_renumbered = std::move(ci2);
-    ci_h = ci_renumbered.get();
   }
 
   g->gather = gather;

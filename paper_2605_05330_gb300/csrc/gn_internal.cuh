@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <functional>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -132,8 +133,8 @@ double host_gamma(const gn_params& p, int k);
 gn_status state_stats(gn_graph* g, const float* x_int, double theta, double* obj, unsigned* nonbin);
 gn_status to_internal(gn_graph* g, const float* x_caller, const float** x_int);
 // implemented in gn_reorder.cu
-gn_status rcm_order_device(gn_graph* g, const std::vector<int32_t>& rp, std::vector<int32_t>& perm,
-                           bool* done);
+gn_status rcm_reorder_device(gn_graph* g, std::vector<int32_t>& rp, std::unique_ptr<int32_t[]>& ci_new,
+                             bool* done);
 // implemented in gn_graph.cu
 gn_status upload_or_alias(gn_graph* g, const void* src, size_t bytes, const void** dev_ptr);
 gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes);

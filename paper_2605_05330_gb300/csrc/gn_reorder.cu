@@ -33,6 +33,7 @@
 
 #include <climits>
 #include <cstring>
+#include <memory>
 
 #include "gn_internal.cuh"
 
@@ -380,15 +381,123 @@ k_rcm(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
   if (rank == 0 && tid == 0) *status = 0;
 }
 
+// ------------------------------------------------------------------------------------------
+// renumbering in the new order, on the device, right after the search: every kernel first reads
+// the search's status and does nothing unless it succeeded (no host round trip in between)
+
+constexpr int kRnTile = 4096;  // row degrees per block of the scan (1024 threads x 4)
+
+// perm[r] = order[n - 1 - r] (the reversal), iperm, and the degrees in the new order
+__global__ void k_rn_perm(int n, const int* __restrict__ status, const int32_t* __restrict__ order,
+                          const int32_t* __restrict__ rp, int32_t* __restrict__ perm, int32_t* __restrict__ iperm,
+                          int32_t* __restrict__ deg) {
+  if (*status != 0) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int o = order[n - 1 - r];
+  perm[r] = o;
+  iperm[o] = r;
+  deg[r] = rp[o + 1] - rp[o];
+}
+
+// sum of each tile of kRnTile degrees
+__global__ void __launch_bounds__(1024) k_rn_tile_sums(int n, const int* __restrict__ status,
+                                                       const int32_t* __restrict__ deg, int32_t* __restrict__ tsum) {
+  if (*status != 0) return;
+  __shared__ int s[32];
+  int v = 0;
+  for (int i = blockIdx.x * kRnTile + threadIdx.x; i < min(n, (blockIdx.x + 1) * kRnTile); i += blockDim.x)
+    v += deg[i];
+  v = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int t = __reduce_add_sync(0xffffffffu, s[threadIdx.x]);
+    if (threadIdx.x == 0) tsum[blockIdx.x] = t;
+  }
+}
+
+// exclusive prefix of the tile sums, in place (one CTA, any number of tiles)
+__global__ void __launch_bounds__(1024) k_rn_tile_scan(int ntiles, const int* __restrict__ status,
+                                                       int32_t* __restrict__ tsum) {
+  if (*status != 0) return;
+  __shared__ int s[64];
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += kRcmThreads) {
+    const int i = base + threadIdx.x;
+    const int v = i < ntiles ? tsum[i] : 0;
+    int2 tot;
+    const int pre = rcm_scan2(v, 0, tot, s).x;
+    if (i < ntiles) tsum[i] = carry + pre;
+    carry += tot.x;
+  }
+}
+
+// the new row pointers: each tile's exclusive prefix from its offset; rp2[n] = nnz
+__global__ void __launch_bounds__(1024) k_rn_rowptr(int n, int32_t nnz, const int* __restrict__ status,
+                                                    const int32_t* __restrict__ deg, const int32_t* __restrict__ toff,
+                                                    int32_t* __restrict__ rp2) {
+  if (*status != 0) return;
+  __shared__ int s[64];
+  constexpr int E = kRnTile / 1024;
+  const int i0 = blockIdx.x * kRnTile + threadIdx.x * E;
+  int d[E], sum = 0;
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    d[t] = i0 + t < n ? deg[i0 + t] : 0;
+    sum += d[t];
+  }
+  int2 tot;
+  int at = toff[blockIdx.x] + rcm_scan2(sum, 0, tot, s).x;
+#pragma unroll
+  for (int t = 0; t < E; ++t)
+    if (i0 + t < n) {
+      rp2[i0 + t] = at;
+      at += d[t];
+    }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rp2[n] = nnz;
+}
+
+// the rows in the new order, their entries renumbered and sorted (rows are short: the search
+// runs only for degrees up to kRcmMaxDeg)
+__global__ void k_rn_rows(int n, const int* __restrict__ status, const int32_t* __restrict__ rp,
+                          const int32_t* __restrict__ ci, const int32_t* __restrict__ perm,
+                          const int32_t* __restrict__ iperm, const int32_t* __restrict__ rp2, int32_t* __restrict__ ci2) {
+  if (*status != 0) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int o = perm[r], a = rp[o], d = rp[o + 1] - a;
+  int32_t* dst = ci2 + rp2[r];
+  for (int k = 0; k < d; ++k) {
+    const int32_t x = iperm[ci[a + k]];
+    int j = k;
+    for (; j > 0 && dst[j - 1] > x; --j) dst[j] = dst[j - 1];
+    dst[j] = x;
+  }
+}
+
+// the renumbered CSR over the handle's (caller-order) one
+__global__ void k_rn_copy(int n, int64_t nnz, const int* __restrict__ status, const int32_t* __restrict__ rp2,
+                          const int32_t* __restrict__ ci2, int32_t* __restrict__ rp, int32_t* __restrict__ ci) {
+  if (*status != 0) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) rp[i] = rp2[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) ci[i] = ci2[i];
+}
+
 // Reverse Cuthill-McKee order of the caller-order CSR already on the device (g->d_row_ptr,
-// g->d_col_idx, validated).  perm[r] = the vertex placed r-th.  *done is false (perm untouched)
-// when the graph is outside the kernel's scope (few vertices, a degree above kRcmMaxDeg), the
-// cluster cannot be launched, or the search stopped (a level past the buffers or the level
-// budget); the host search then gives the same order.
-gn_status rcm_order_device(gn_graph* g, const std::vector<int32_t>& rp, std::vector<int32_t>& perm,
-                           bool* done) {
+// g->d_col_idx, validated), and the renumbering in it, all on the device.  On success (*done):
+// g->d_perm and g->d_iperm hold the order (perm[r] = the caller's vertex placed r-th after the
+// reversal), g->d_row_ptr and g->d_col_idx the renumbered CSR (rows sorted), and rp and *ci_new
+// the same CSR on the host.  *done is false (nothing changed) when the graph is outside the
+// search's scope (few vertices, a degree above kRcmMaxDeg), the cluster cannot be launched, or
+// the search stopped (a level past the buffers or the level budget); the host then computes the
+// same order and renumbers.
+gn_status rcm_reorder_device(gn_graph* g, std::vector<int32_t>& rp, std::unique_ptr<int32_t[]>& ci_new,
+                             bool* done) {
   *done = false;
   const int n = g->n;
+  const int64_t nnz = g->nnz;
   if (n < kRcmMinVertices) return GN_OK;
   // degrees and a stable counting sort by degree, split over the host threads
   const int nt = std::max(1, std::min(host_threads(), n / 4096));
@@ -440,16 +549,23 @@ gn_status rcm_order_device(gn_graph* g, const std::vector<int32_t>& rp, std::vec
   }
   if (clusters < 1) return GN_OK;
 
-  int32_t* scratch = nullptr;  // by_deg, par, order, status
-  GN_CUDA(cudaMalloc(&scratch, sizeof(int32_t) * (3 * (size_t)n + 1)));
+  // scratch: by_deg, par, order, degrees, new row pointers, tile sums, new rows, status
+  const int ntiles = (n + kRnTile - 1) / kRnTile;
+  const size_t words = 4 * (size_t)n + ((size_t)n + 1) + (size_t)ntiles + (size_t)std::max<int64_t>(nnz, 1) + 1;
+  int32_t* scratch = nullptr;
+  GN_CUDA(cudaMalloc(&scratch, sizeof(int32_t) * words));
   struct Free {
     int32_t* p;
     ~Free() { cudaFree(p); }
   } free_scratch{scratch};
   int32_t* d_by_deg = scratch;
-  int32_t* d_par = scratch + n;
-  int32_t* d_order = scratch + 2 * (size_t)n;
-  int* d_status = scratch + 3 * (size_t)n;
+  int32_t* d_par = d_by_deg + n;
+  int32_t* d_order = d_par + n;
+  int32_t* d_deg = d_order + n;
+  int32_t* d_rp2 = d_deg + n;
+  int32_t* d_tsum = d_rp2 + ((size_t)n + 1);
+  int32_t* d_ci2 = d_tsum + ntiles;
+  int* d_status = d_ci2 + std::max<int64_t>(nnz, 1);
   GN_CUDA(cudaMemcpyAsync(d_by_deg, by_deg.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaMemsetAsync(d_status, 0xff, sizeof(int), g->stream));
   // the search stops paying once its levels cost more than the host's per-vertex work
@@ -458,13 +574,35 @@ gn_status rcm_order_device(gn_graph* g, const std::vector<int32_t>& rp, std::vec
                                                  d_par, d_order, d_status);
   GN_LAUNCHED();
   GN_CUDA(cudaGetLastError());
-  std::vector<int32_t> order(n);
+  const unsigned gn_ = (unsigned)((n + 255) / 256);
+  k_rn_perm<<<gn_, 256, 0, g->stream>>>(n, d_status, d_order, g->d_row_ptr, g->d_perm, g->d_iperm, d_deg);
+  GN_LAUNCHED();
+  k_rn_tile_sums<<<ntiles, 1024, 0, g->stream>>>(n, d_status, d_deg, d_tsum);
+  GN_LAUNCHED();
+  k_rn_tile_scan<<<1, kRcmThreads, 0, g->stream>>>(ntiles, d_status, d_tsum);
+  GN_LAUNCHED();
+  k_rn_rowptr<<<ntiles, 1024, 0, g->stream>>>(n, (int32_t)nnz, d_status, d_deg, d_tsum, d_rp2);
+  GN_LAUNCHED();
+  k_rn_rows<<<gn_, 256, 0, g->stream>>>(n, d_status, g->d_row_ptr, g->d_col_idx, g->d_perm, g->d_iperm, d_rp2,
+                                        d_ci2);
+  GN_LAUNCHED();
+  k_rn_copy<<<std::min<unsigned>(gn_, 1024u), 256, 0, g->stream>>>(n, nnz, d_status, d_rp2, d_ci2, g->d_row_ptr,
+                                                                  g->d_col_idx);
+  GN_LAUNCHED();
+  GN_CUDA(cudaGetLastError());
   int status = -1;
-  GN_CUDA(cudaMemcpyAsync(order.data(), d_order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, g->stream));
   GN_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
   GN_CUDA(cudaStreamSynchronize(g->stream));
   if (status != 0) return GN_OK;
-  perm.assign(order.rbegin(), order.rend());
+  // the renumbered CSR on the host too (the halo blocks are built from it)
+  std::vector<int32_t> rp2(n + 1);
+  std::unique_ptr<int32_t[]> ci2(new int32_t[(size_t)std::max<int64_t>(nnz, 1)]);
+  GN_CUDA(cudaMemcpyAsync(rp2.data(), d_rp2, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, g->stream));
+  if (nnz > 0)
+    GN_CUDA(cudaMemcpyAsync(ci2.get(), d_ci2, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  rp.swap(rp2);
+  ci_new = std::move(ci2);
   *done = true;
   return GN_OK;
 }
