@@ -161,6 +161,9 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
         whi = std::max(whi, j >> 6);
       }
       std::vector<int32_t>& xb = ext[b];
+      size_t count = 0;
+      for (int wd = wlo; wd <= whi; ++wd) count += (size_t)__builtin_popcountll(bits[wd]);
+      xb.reserve(count);
       int64_t sec = 0, last = -1;
       for (int wd = wlo; wd <= whi; ++wd) {
         uint64_t m = bits[wd];
@@ -216,21 +219,36 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
   if (push) {
     parallel_items(nb, [&](int o, int) {
-      {
-        for (int c = 0; c < nb; ++c) {
-          const std::vector<int32_t>& xc = ext[c];
-          const size_t t0 = std::lower_bound(xc.begin(), xc.end(), part[o]) - xc.begin();
-          const size_t t1 = std::lower_bound(xc.begin() + t0, xc.end(), part[o + 1]) - xc.begin();
-          for (size_t t = t0; t < t1; ++t)
-            sends[o].push_back({(int32_t)(inbox_off[c] + (int64_t)t), xc[t] - part[o]});
-        }
+      std::vector<std::pair<size_t, size_t>> run(nb);  // o's run in each consumer's halo
+      size_t total = 0;
+      for (int c = 0; c < nb; ++c) {
+        const std::vector<int32_t>& xc = ext[c];
+        const size_t t0 = std::lower_bound(xc.begin(), xc.end(), part[o]) - xc.begin();
+        const size_t t1 = std::lower_bound(xc.begin() + t0, xc.end(), part[o + 1]) - xc.begin();
+        run[c] = {t0, t1};
+        total += t1 - t0;
       }
+      std::vector<std::pair<int32_t, int32_t>>& so = sends[o];
+      so.resize(total);
+      size_t at = 0;
+      for (int c = 0; c < nb; ++c)
+        for (size_t t = run[c].first; t < run[c].second; ++t)
+          so[at++] = {(int32_t)(inbox_off[c] + (int64_t)t), ext[c][t] - part[o]};
     });
   }
 
   // pass 1, per CTA: rows into interior / boundary / heavy, slices, chunks, send pieces and
-  // the block layout
-  std::vector<std::vector<unsigned char>> blocks(nb);
+  // the block layout (the plan; pass 2 writes the blocks straight into the upload buffer)
+  struct Plan {
+    HaloHeader H;
+    std::vector<int2> meta;
+    std::vector<short> srow;
+    std::vector<int> hmeta, hchunk;
+    std::vector<int32_t> dep;
+    std::vector<int4> pieces;
+    std::vector<uint16_t> src;
+  };
+  std::vector<Plan> plans(nb);
   parallel_items(nb, [&](int b, int) {
     {
       const int rb = part[b], re = part[b + 1], nr = re - rb;
@@ -343,30 +361,32 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       H.off_x = (int)off;
       if (!push) off = align16(off + 4 * xb.size());
       H.bytes = (int)off;
-      std::vector<unsigned char>& B = blocks[b];
-      B.assign(off, 0);
-      memcpy(B.data(), &H, sizeof H);
-      if (ns) memcpy(B.data() + H.off_meta, meta.data(), sizeof(int2) * ns);
-      if (ns) memcpy(B.data() + H.off_srow, srow.data(), sizeof(short) * 32 * (size_t)ns);
-      if (!hmeta.empty()) memcpy(B.data() + H.off_hmeta, hmeta.data(), 4 * hmeta.size());
-      if (!dep.empty()) memcpy(B.data() + H.off_dep, dep.data(), 4 * dep.size());
-      if (!hchunk.empty()) memcpy(B.data() + H.off_hchunk, hchunk.data(), 4 * hchunk.size());
-      if (!pieces.empty()) memcpy(B.data() + H.off_piece, pieces.data(), sizeof(int4) * pieces.size());
-      if (!src.empty()) memcpy(B.data() + H.off_src, src.data(), 2 * src.size());
-      if (!push && !xb.empty()) memcpy(B.data() + H.off_x, xb.data(), 4 * xb.size());
+      Plan& P = plans[b];
+      P.H = H;
+      P.meta = std::move(meta);
+      P.srow = std::move(srow);
+      P.hmeta = std::move(hmeta);
+      P.hchunk = std::move(hchunk);
+      P.dep = std::move(dep);
+      P.pieces = std::move(pieces);
+      P.src = std::move(src);
     }
   });
   int lx_max = 0;
   size_t blk_max = 0;
   for (int b = 0; b < nb; ++b) {
     lx_max = std::max(lx_max, (int)ext[b].size());
-    blk_max = std::max(blk_max, blocks[b].size());
+    blk_max = std::max(blk_max, (size_t)plans[b].H.bytes);
   }
   const int Lp = (lx_max + 3) & ~3;
   const int zero_id = R + Lp;  // 32 zero slots from here, one per bank
   const size_t floats = (size_t)6 * R + Lp + 32;
   const size_t smem = 4 * floats + blk_max;
   if (zero_id + 31 > 65535 || smem > smem_limit || R > 32767) return GN_OK;  // does not fit
+  std::vector<int64_t> hoff(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) hoff[b + 1] = hoff[b] + plans[b].H.bytes;
+  const size_t blob_bytes = (size_t)std::max<int64_t>(hoff[nb], 16);
+  std::unique_ptr<unsigned char[]> blob(new unsigned char[blob_bytes]);
 
   // pass 2, per CTA: the 16-bit local ids (own row r -> r, external halo t -> R + t,
   // padding -> the zero slot)
@@ -390,16 +410,31 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     std::vector<uint16_t>* bucket = X.bucket;
     {
       const int rb = part[b], re = part[b + 1];
-      std::vector<unsigned char>& B = blocks[b];
-      HaloHeader* H = reinterpret_cast<HaloHeader*>(B.data());
+      // the block: zeros, then the plan's header and sections
+      unsigned char* B = blob.get() + hoff[b];
+      {
+        const Plan& P = plans[b];
+        const HaloHeader& PH = P.H;
+        memset(B, 0, PH.bytes);
+        memcpy(B, &PH, sizeof PH);
+        if (PH.ns) memcpy(B + PH.off_meta, P.meta.data(), sizeof(int2) * PH.ns);
+        if (PH.ns) memcpy(B + PH.off_srow, P.srow.data(), sizeof(short) * 32 * (size_t)PH.ns);
+        if (!P.hmeta.empty()) memcpy(B + PH.off_hmeta, P.hmeta.data(), 4 * P.hmeta.size());
+        if (!P.dep.empty()) memcpy(B + PH.off_dep, P.dep.data(), 4 * P.dep.size());
+        if (!P.hchunk.empty()) memcpy(B + PH.off_hchunk, P.hchunk.data(), 4 * P.hchunk.size());
+        if (!P.pieces.empty()) memcpy(B + PH.off_piece, P.pieces.data(), sizeof(int4) * P.pieces.size());
+        if (!P.src.empty()) memcpy(B + PH.off_src, P.src.data(), 2 * P.src.size());
+        if (!push && !ext[b].empty()) memcpy(B + PH.off_x, ext[b].data(), 4 * ext[b].size());
+      }
+      HaloHeader* H = reinterpret_cast<HaloHeader*>(B);
       H->zero_id = zero_id;
       for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = (int32_t)t;
       auto lid = [&](int j) -> uint16_t {
         return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
       };
-      const int2* meta = reinterpret_cast<const int2*>(B.data() + H->off_meta);
-      const short* srow = reinterpret_cast<const short*>(B.data() + H->off_srow);
-      uint16_t* sell = reinterpret_cast<uint16_t*>(B.data() + H->off_sell);
+      const int2* meta = reinterpret_cast<const int2*>(B + H->off_meta);
+      const short* srow = reinterpret_cast<const short*>(B + H->off_srow);
+      uint16_t* sell = reinterpret_cast<uint16_t*>(B + H->off_sell);
       // Every lane's row may list its entries in any order: colour the slice (color_slice) so
       // that each column's real entries lie in distinct banks, then pad each lane's empty
       // columns with the zero slot of a bank no real entry of that column uses (all padding of
@@ -454,9 +489,9 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
             sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = lids[l][t];
           }
       }
-      const int* hm = reinterpret_cast<const int*>(B.data() + H->off_hmeta);
-      const int* hc = reinterpret_cast<const int*>(B.data() + H->off_hchunk);
-      uint16_t* hl = reinterpret_cast<uint16_t*>(B.data() + H->off_hl);
+      const int* hm = reinterpret_cast<const int*>(B + H->off_hmeta);
+      const int* hc = reinterpret_cast<const int*>(B + H->off_hchunk);
+      uint16_t* hl = reinterpret_cast<uint16_t*>(B + H->off_hl);
       // heavy rows: entries dealt round-robin over the banks, so each group of 32 consecutive
       // entries (one gather instruction of sum_chunk) spreads over the banks
       for (int h = 0; h < H->nheavy; ++h) {
@@ -476,14 +511,8 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       }
     }
   });
-  std::vector<int64_t> hoff(nb + 1, 0);
-  for (int b = 0; b < nb; ++b) hoff[b + 1] = hoff[b] + (int64_t)blocks[b].size();
-  std::vector<unsigned char> blob((size_t)std::max<int64_t>(hoff[nb], 16));
-  parallel_for(nb, 8, [&](int lo, int hi, int) {
-    for (int b = lo; b < hi; ++b) memcpy(blob.data() + hoff[b], blocks[b].data(), blocks[b].size());
-  });
   GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
-  GN_CUDA(cudaMalloc(&g->d_hblob, blob.size()));
+  GN_CUDA(cudaMalloc(&g->d_hblob, blob_bytes));
   if (push) {
     g->inbox_len = std::max<int64_t>(inbox_off[nb], 4);
     GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 2 * (size_t)g->inbox_len));
@@ -491,7 +520,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   }
   g->halo_push = push;
   GN_CUDA(cudaMemcpyAsync(g->d_hoff, hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, g->stream));
-  GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, g->stream));
+  GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.get(), blob_bytes, cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaStreamSynchronize(g->stream));
   g->halo_pad = Lp;
   g->rows_pad_halo = R;
