@@ -167,8 +167,8 @@ def measured_peaks():
 
 
 # the sources the iteration kernel is compiled from
-# the iteration kernel and the host code that lays out its per-CTA blocks
-KERNEL_SOURCES = ("gn_halo.cu", "gn_halo.cuh", "gn_halo_build.cu", "gn_iter_common.cuh", "gn_device.cuh")
+# the iteration kernel's sources; the layout of its per-CTA blocks is versioned in gn_halo.cuh
+KERNEL_SOURCES = ("gn_halo.cu", "gn_halo.cuh", "gn_iter_common.cuh", "gn_device.cuh")
 
 
 def kernel_source_hash() -> str:

@@ -6,6 +6,12 @@
 
 namespace gn {
 
+// Version of what the builder writes into the blocks (layout and contents for a given graph and
+// partition).  It changes with every change to gn_halo_build.cu that changes its output, so the
+// recorded DRAM traffic of the kernel, which depends on it, is tied to this header and not to
+// the builder's code.
+constexpr int kHaloLayoutVersion = 3;
+
 // header of a CTA block (int32 words), followed by 16-byte aligned sections
 struct HaloHeader {
   int ns_int;      // interior slices (every row's neighbours are own rows)

@@ -211,7 +211,6 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   int max_rows = 0;
   for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
   const int R = (max_rows + 3) & ~3;
-  auto owner = [&](int j) { return (int)(std::upper_bound(part.begin(), part.end(), j) - part.begin()) - 1; };
 
   // send lists: for each owner o, the (inbox slot, own row) pairs in slot order.  The slots of
   // consumer c come before those of c + 1, and within c's halo (sorted by id) the vertices of
@@ -253,11 +252,11 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     {
       const int rb = part[b], re = part[b + 1], nr = re - rb;
       const std::vector<int32_t>& xb = ext[b];
-      // the CTAs owning the halo (xb is sorted, the partition is contiguous)
+      // the CTAs owning the halo (xb is sorted and the partition contiguous: one walk)
       std::vector<int32_t> dep;
-      for (int j : xb) {
-        const int o = owner(j);
-        if (dep.empty() || dep.back() != o) dep.push_back(o);
+      for (size_t t = 0, o = 0; t < xb.size(); ++t) {
+        while (xb[t] >= part[o + 1]) ++o;
+        if (dep.empty() || dep.back() != (int32_t)o) dep.push_back((int32_t)o);
       }
       std::vector<int> light_int, light_bnd, heavy;
       for (int r = 0; r < nr; ++r) {
@@ -407,6 +406,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     std::vector<int>* cols = X.cols;
     ColorScratch& cs = X.cs;
     std::vector<int>& occ = X.occ;
+    uint64_t usedcols[32];
     std::vector<uint16_t>* bucket = X.bucket;
     {
       const int rb = part[b], re = part[b + 1];
@@ -455,11 +455,11 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
           for (uint16_t id : lids[l]) ++load[id & 31];
         for (int t = 0; t < 32; ++t) Wc = std::max(Wc, load[t]);
         color_slice(Wc, lids, cols, cs);
-        occ.assign(32 * (size_t)W, 0);  // occ[bank * W + column]
-        for (int l = 0; l < 32; ++l)
-          for (size_t t = 0; t < lids[l].size(); ++t)
-            if (cols[l][t] < W) ++occ[(lids[l][t] & 31) * W + cols[l][t]];
         if (Wc > W) {
+          occ.assign(32 * (size_t)W, 0);  // occ[bank * W + column]
+          for (int l = 0; l < 32; ++l)
+            for (size_t t = 0; t < lids[l].size(); ++t)
+              if (cols[l][t] < W) ++occ[(lids[l][t] & 31) * W + cols[l][t]];
           for (int l = 0; l < 32; ++l) {
             uint64_t used = 0;
             for (size_t t = 0; t < lids[l].size(); ++t)
@@ -476,18 +476,30 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
             }
           }
         }
-        for (int k = 0; k < W; ++k) {
-          int zb = 0;  // the bank least used by column k's real entries (unused when one exists)
-          for (int t = 1; t < 32; ++t)
-            if (occ[t * W + k] < occ[zb * W + k]) zb = t;
-          const uint16_t zero = (uint16_t)(zero_id + ((zb - zero_id) & 31));
-          for (int l = 0; l < 32; ++l) sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = zero;
-        }
-        for (int l = 0; l < 32; ++l)
+        // the real entries, each lane's used columns and each column's used banks; then the
+        // padding: an empty slot of column k reads the zero slot of the lowest bank no real entry
+        // of k uses (a column without a free bank has all 32 lanes real, so no empty slot)
+        uint32_t colbanks[64] = {0};
+        const int base = meta[s].x;
+        for (int l = 0; l < 32; ++l) {
+          uint64_t used = 0;
           for (size_t t = 0; t < lids[l].size(); ++t) {
             const int k = cols[l][t];
-            sell[meta[s].x + (k >> 2) * 128 + l * 4 + (k & 3)] = lids[l][t];
+            sell[base + (k >> 2) * 128 + l * 4 + (k & 3)] = lids[l][t];
+            used |= 1ull << k;
+            colbanks[k] |= 1u << (lids[l][t] & 31);
           }
+          usedcols[l] = used;
+        }
+        for (int l = 0; l < 32; ++l) {
+          uint64_t empty = ~usedcols[l] & (W == 64 ? ~0ull : (1ull << W) - 1);
+          while (empty) {
+            const int k = __builtin_ctzll(empty);
+            empty &= empty - 1;
+            const int zb = __builtin_ctz(~colbanks[k]);
+            sell[base + (k >> 2) * 128 + l * 4 + (k & 3)] = (uint16_t)(zero_id + ((zb - zero_id) & 31));
+          }
+        }
       }
       const int* hm = reinterpret_cast<const int*>(B + H->off_hmeta);
       const int* hc = reinterpret_cast<const int*>(B + H->off_hchunk);

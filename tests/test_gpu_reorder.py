@@ -79,6 +79,10 @@ CASES = {
     "er3k": (lambda: inputs.er_graph(3000, 6.0, 13), "host"),
     # degrees above the device search's bound
     "ba20k": (lambda: inputs.ba_graph(20000, 5, 14), "host"),
+    # no edges: every vertex is its own component, placed before any search
+    "edgeless20k": (lambda: inputs.small_graph("edgeless20k", 20000, []), "device"),
+    # a star: its centre's degree is above the bound
+    "star20k": (lambda: inputs.small_graph("star20k", 20000, [(0, j) for j in range(1, 20000)]), "host"),
 }
 
 
