@@ -181,9 +181,10 @@ int64_t gn_num_entries(const gn_graph* g);
 gn_status gn_vertex_order(const gn_graph* g, int32_t* order);
 
 #define GN_ORDER_FROM_HOST 1    /* the order was computed on the host */
-#define GN_ORDER_FROM_DEVICE 2  /* by the single-CTA breadth-first search on the device (RCM on
-                                   graphs of >= 16,384 vertices and degrees <= 64 whose levels fit
-                                   its shared-memory buffers; the same order as the host's) */
+#define GN_ORDER_FROM_DEVICE 2  /* by the breadth-first search of one thread-block cluster on the
+                                   device (RCM on graphs of >= 16,384 vertices and degrees <= 254
+                                   whose levels fit its shared-memory buffers and level budget;
+                                   the same order as the host's), renumbered there too */
 /* Where the handle's internal order was computed: GN_ORDER_FROM_*, 0 without reordering or for
  * NULL. */
 int gn_vertex_order_source(const gn_graph* g);

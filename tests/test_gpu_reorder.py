@@ -1,6 +1,6 @@
 """The handle's internal vertex orders against their definitions.  Reverse Cuthill-McKee is
 searched on the device when the graph is in the search kernel's scope (at least 16,384 vertices,
-degrees up to 64, levels that fit its shared-memory buffers, a level budget) and on the host
+degrees up to 254, levels that fit its shared-memory buffers, a level budget) and on the host
 otherwise; either way the order is the one defined below, element for element.  Descending
 degree is a stable sort."""
 import numpy as np
