@@ -129,12 +129,6 @@ gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes) {
   return GN_OK;
 }
 
-// Reverse Cuthill-McKee over every component (BFS from a minimum-degree vertex, neighbours
-// visited in increasing degree, ties in the order met), reversed.  perm[new] = old.  The
-// vertices are bucketed by degree (a stable counting sort); each BFS step places its new
-// neighbours by a stable insertion sort on degree.  key[v] holds the degree with the sign bit
-// set once v is placed, so each neighbour costs one random access (the traversal is bound by
-// those on graphs with random labels).
 // ---- the host worker pool behind parallel_for
 //
 // Workers start on the first multi-block job and stay, parked on a condition variable, for the
@@ -207,6 +201,13 @@ void run_parts(int parts, const std::function<void(int)>& f) {
   P->job = nullptr;
 }
 
+// Reverse Cuthill-McKee over every component (BFS from a minimum-degree vertex, neighbours
+// visited in increasing degree, ties in the order met), reversed, on the host: the order the
+// device search (gn_reorder.cu) reproduces, used for graphs outside its scope.  perm[new] = old.
+// The vertices are bucketed by degree (a stable counting sort); each BFS step places its new
+// neighbours by a stable insertion sort on degree.  key[v] holds the degree with the sign bit
+// set once v is placed, so each neighbour costs one random access (the traversal is bound by
+// those on graphs with random labels).
 static void rcm_order(int n, const std::vector<int32_t>& rp, const int32_t* ci, std::vector<int32_t>& perm) {
   perm.clear();
   perm.reserve(n);
