@@ -40,13 +40,22 @@ static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int
   for (int l = 0; l < 32; ++l) E += (int)lid[l].size();
   std::vector<int>& at_l = cs.at_l;
   std::vector<int>& at_b = cs.at_b;
-  std::vector<uint64_t>& ul = cs.used_l;
-  std::vector<uint64_t>& ub = cs.used_b;
   int* elane = (cs.elane.resize(E), cs.elane.data());
   int* ebank = (cs.ebank.resize(E), cs.ebank.data());
   int* ecol = (cs.ecol.resize(E), cs.ecol.data());
-  ul.assign(32 * (size_t)nw, 0);
-  ub.assign(32 * (size_t)nw, 0);
+  // the used-colour sets: on the stack for up to 64 colours (every slice in practice)
+  uint64_t ul_small[32], ub_small[32];
+  uint64_t* ul = ul_small;
+  uint64_t* ub = ub_small;
+  if (nw > 1) {
+    cs.used_l.assign(32 * (size_t)nw, 0);
+    cs.used_b.assign(32 * (size_t)nw, 0);
+    ul = cs.used_l.data();
+    ub = cs.used_b.data();
+  } else {
+    for (int i = 0; i < 32; ++i) ul_small[i] = ub_small[i] = 0;
+  }
+  const uint64_t last_mask = (W & 63) ? (1ull << (W & 63)) - 1 : ~0ull;  // colours < W in the last word
   bool tables = false;
   // the lowest colour free at a vertex (one exists below W: its edges so far are fewer than W)
   auto lowest_free = [nw](const uint64_t* u) {
@@ -80,10 +89,9 @@ static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int
       // the lowest colour free at both ends when there is one below W
       int a = -1;
       for (int w = 0; w < nw && a < 0; ++w) {
-        const uint64_t both = ~(ul[(size_t)l * nw + w] | ub[(size_t)b * nw + w]);
+        const uint64_t both = ~(ul[(size_t)l * nw + w] | ub[(size_t)b * nw + w]) & (w + 1 < nw ? ~0ull : last_mask);
         if (both) a = w * 64 + __builtin_ctzll(both);
       }
-      if (a >= W) a = -1;
       if (a < 0) {
         // a free at l, c free at b: swap a and c along the a/c path from b
         if (!tables) {
