@@ -29,6 +29,9 @@
 // buffers hold, a search past the level budget or a degree above the bound returns a status and
 // the host computes the order itself.  Every loop is bounded by n, the capacities or the level
 // budget; every exit is taken by all CTAs together, at the same point.
+//
+// After the search, six small kernels renumber the CSR in the new order on the device (the host
+// keeps a copy for its block builder); each does nothing unless the search succeeded.
 #include <cooperative_groups.h>
 
 #include <climits>
