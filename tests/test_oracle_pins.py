@@ -522,3 +522,63 @@ def test_mpnn_reference_gradient_against_central_differences():
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[idx]) <= 1e-5 * max(1.0, abs(g[idx])), (idx, fd, g[idx])
     assert p.shape == (inst.n,) and np.all((p > 0) & (p < 1))
+
+
+@pytest.mark.parametrize("a,b,gam", [(0.3, 0.7, 1.2), (0.9, 0.05, 0.8), (0.25, 0.25, 1.5)])
+def test_energy_on_k2_at_fractional_states(a, b, gam):
+    """Sec. 3: E~(y) = 1/2 y^T (I + gamma A) y - v^T y with y = v (.) x.  On K2 with w = (4, 1),
+    v = (2, 1) and y = (2a, b), worked by hand: E~ = 1/2 (4a^2 + b^2 + 4 gamma a b) - (4a + b).
+    Away from a binary state the gamma term is not zero, so a dropped or doubled gamma, or a
+    wrong weight exponent, changes the value."""
+    inst = inputs.small_graph("K2", 2, [(0, 1)], [4.0, 1.0])
+    want = 0.5 * (4 * a * a + b * b + 4 * gam * a * b) - (4 * a + b)
+    got = oracle.energy(inst.row_ptr, inst.col_idx, inst.w, gam, np.array([a, b]))
+    assert got == pytest.approx(want, rel=1e-14, abs=1e-15)
+
+
+@pytest.mark.parametrize("name,n,edges,d", [
+    ("C7", 7, [(i, (i + 1) % 7) for i in range(7)], 2),
+    ("K4", 4, [(i, j) for i in range(4) for j in range(i + 1, 4)], 3),
+    ("Q3", 8, [(i, i ^ (1 << k)) for i in range(8) for k in range(3) if i < i ^ (1 << k)], 3),
+])
+@pytest.mark.parametrize("c,gam,wv", [(0.2, 1.5, 1.0), (0.6, 0.9, 9.0)])
+def test_energy_uniform_state_on_regular_graphs(name, n, edges, d, c, gam, wv):
+    """Sec. 3 energy at the uniform state x = c 1 of a d-regular graph with uniform weight w
+    (the atom of App. A): y = sqrt(w) c, (I + gamma A) y = (1 + gamma d) y, so
+    E~ = n w (c^2 (1 + gamma d) / 2 - c)."""
+    inst = inputs.small_graph(name, n, edges, [wv] * n)
+    want = n * wv * (0.5 * c * c * (1 + gam * d) - c)
+    got = oracle.energy(inst.row_ptr, inst.col_idx, inst.w, gam, np.full(n, c))
+    assert got == pytest.approx(want, rel=1e-14)
+
+
+def test_extract_is_failure_branches():
+    """Sec. 2 (independent sets) and Sec. 6 (valid MIS after rounding): on the path 0-1-2-3-4
+    the rounding of (1, 0, 1, 0, 1) is a maximal independent set; raising vertex 1 above 1/2
+    puts the edge 0-1 inside S (not independent); (1, 0, 0, 0, 1) leaves vertex 2 with no
+    neighbour in S (not maximal); exactly 1/2 rounds out."""
+    inst = inputs.small_graph("P5", 5, [(0, 1), (1, 2), (2, 3), (3, 4)], [1.0, 2.0, 3.0, 4.0, 5.0])
+    rp, ci, w = inst.row_ptr, inst.col_idx, inst.w
+    st, mask, mem, W = oracle.extract_is(rp, ci, w, np.array([0.9, 0.1, 0.8, 0.2, 0.7]))
+    assert st == "OK" and list(mem) == [0, 2, 4] and W == 9.0
+    st, mask, mem, W = oracle.extract_is(rp, ci, w, np.array([0.9, 0.6, 0.8, 0.2, 0.7]))
+    assert st == "ERR_NOT_INDEPENDENT" and list(mask) == [1, 1, 1, 0, 1] and W == 11.0
+    st, mask, mem, W = oracle.extract_is(rp, ci, w, np.array([0.9, 0.1, 0.5, 0.2, 0.7]))
+    assert st == "WARN_NOT_MAXIMAL" and list(mem) == [0, 4] and W == 6.0
+    # a dependent set is reported as such even when it is also not maximal elsewhere
+    st, *_ = oracle.extract_is(rp, ci, w, np.array([0.9, 0.6, 0.0, 0.0, 0.0]))
+    assert st == "ERR_NOT_INDEPENDENT"
+
+
+def test_stability_exact_value():
+    """Thm. 4: stab_{gamma,w}(M) = gamma min_{i not in M} sum_{j in N(i) cap M} sqrt(w_j / w_i).
+    Path 0-1-2-3-4 with w = (4, 1, 9, 16, 4) and M = {0, 3}: vertex 1 sees sqrt(4/1) = 2 (its
+    neighbour 2 is not in M), vertex 2 sees sqrt(16/9) = 4/3, vertex 4 sees sqrt(16/4) = 2, so
+    stab = 4 gamma / 3.  Summing over all neighbours would give 5 gamma / 3, a maximum 2 gamma,
+    inverted ratios gamma / 2."""
+    inst = inputs.small_graph("P5", 5, [(0, 1), (1, 2), (2, 3), (3, 4)], [4.0, 1.0, 9.0, 16.0, 4.0])
+    mask = np.array([1, 0, 0, 1, 0], dtype=np.uint8)
+    for gam in (1.0, 1.5):
+        got = oracle.stability(inst.row_ptr, inst.col_idx, inst.w, gam, mask)
+        assert got == pytest.approx(4.0 * gam / 3.0, rel=1e-15)
+    assert oracle.stability(inst.row_ptr, inst.col_idx, inst.w, 1.5, np.ones(5, np.uint8)) == math.inf
