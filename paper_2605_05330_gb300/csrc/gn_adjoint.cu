@@ -44,6 +44,24 @@ struct RecordState {
 
 static constexpr int kAdjThreads = 256;
 
+// The recorded forward keeps its states as plain float pairs in FP32's range (the log-space
+// adjoint below reads y = hi + lo); a vertex below FP32's smallest normal contributes nothing to
+// the gradient.  Otherwise the arithmetic of gn_run's update: d = y + gamma s, x' = y / d,
+// y' = v x', the safe division at d <= 1e-9.
+__device__ __forceinline__ void step_pair(dev::f2& y, const dev::f2 v, float& x, float sn, dev::f2 gam,
+                                          unsigned long long& hits) {
+  dev::f2 p = dev::two_prod(gam.hi, sn);
+  p.lo = dev::ffma(gam.lo, sn, p.lo);
+  dev::f2 d = dev::two_sum(y.hi, p.hi);
+  d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(y.lo, p.lo)));
+  const bool ok = d.hi > kSafeDiv;
+  const dev::f2 q = dev::div_f2(y, ok ? d : dev::f2{1.0f, 0.0f});
+  const dev::f2 xn = ok ? q : dev::f2{0.5f, 0.0f};
+  hits += ok ? 0ull : 1ull;
+  y = dev::mul_f2(v, xn);
+  x = xn.hi;
+}
+
 // one forward step, thread per row: y_out = v y_in / ((I + gamma A) y_in) (float pairs)
 __global__ void k_step(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                        const float* __restrict__ vh, const float* __restrict__ vl, float2 gam,
@@ -56,8 +74,7 @@ __global__ void k_step(int n, const int32_t* __restrict__ rp, const int32_t* __r
   dev::f2 y = {yh[i], yl[i]};
   float x = 0.0f;
   unsigned long long h = 0;
-  CheckAcc acc;
-  update_one(y, dev::f2{vh[i], vl[i]}, x, s, dev::f2{gam.x, gam.y}, false, 0.0f, 0.0f, 1.0f, h, acc);
+  step_pair(y, dev::f2{vh[i], vl[i]}, x, s, dev::f2{gam.x, gam.y}, h);
   oh[i] = y.hi;
   ol[i] = y.lo;
   if (x_out) x_out[i] = x;
@@ -211,6 +228,7 @@ gn_status record_forward(gn_graph* g, int k_start, int k_end, const gn_params& p
   // final state where gn_run leaves it
   GN_CUDA(cudaMemcpyAsync(g->d_y[0], ah, nb, cudaMemcpyDeviceToDevice, g->stream));
   GN_CUDA(cudaMemcpyAsync(g->d_ylo, al, nb, cudaMemcpyDeviceToDevice, g->stream));
+  GN_CUDA(cudaMemsetAsync(g->d_yexp, 0, nb, g->stream));  // plain float pairs: no scaled rows
   GN_CUDA(cudaMemcpyAsync(r->xT, g->d_x, nb, cudaMemcpyDeviceToDevice, g->stream));
   g->state_parity = 0;
   GN_CUDA(cudaMemcpyAsync(out, g->d_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, g->stream));

@@ -213,14 +213,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
       const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
       CheckAcc acc;
       for (int i = tid; i < n; i += blockDim.x) {
-        dev::f2 y = {s_yh[i], s_yl[i]};
-        float x = s_x[i];
+        Own o = {s_yh[i], s_yl[i], s_x[i]};
         float sn;
         if (kind == GN_INSTANCE_CSR) {
           sn = s_sum[i];
         } else {
           const int r = i / kk, c = i - r * kk;
-          const float yv = y.hi;
+          const float yv = o.pub;
           // (R_r - y) + (C_c - y) in float pairs
           dev::f2 a = dev::two_sum(s_rh[r], -yv);
           a.lo = dev::fadd(a.lo, s_rl[r]);
@@ -229,11 +228,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
           const dev::f2 t = dev::two_sum(a.hi, b.hi);
           sn = dev::fadd(t.hi, dev::fadd(t.lo, dev::fadd(a.lo, b.lo)));
         }
-        update_one(y, dev::f2{s_vh[i], s_vl[i]}, x, sn, gam, check, check ? P.w[v0 + i] : 0.0f, th_lo,
-                   th_hi, hits, acc);
-        s_yh[i] = y.hi;
-        s_yl[i] = y.lo;
-        s_x[i] = x;
+        update_one(o, dev::f2{s_vh[i], s_vl[i]}, sn, gam, check, check ? P.w[v0 + i] : 0.0f, th_lo, th_hi, hits,
+                   acc);
+        s_yh[i] = o.pub;
+        s_yl[i] = o.aux;
+        s_x[i] = o.xs;
       }
       __syncthreads();
       if (check) {
@@ -256,7 +255,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
       }
     }
     // ---- results (the last check's residual sum and energy: summed once, here)
-    for (int i = tid; i < n; i += blockDim.x) P.x[v0 + i] = s_x[i];
+    for (int i = tid; i < n; i += blockDim.x) P.x[v0 + i] = own_x(Own{s_yh[i], s_yl[i], s_x[i]}, s_vh[i]);
     const dev::f2 l1s = block_sum_pair(dev::f2{last_l1, 0.0f}, s_ph, s_pl);
     const dev::f2 ens = block_sum_pair(dev::f2{last_en, 0.0f}, s_ph, s_pl);
     unsigned long long h = dev::warp_sum_ull(hits);

@@ -306,7 +306,7 @@ extern "C" void gn_destroy(gn_graph* g) {
   if (g->stream) cudaStreamSynchronize(g->stream);
   gn_free_record(g);
   if (g->cta) gn_batch_destroy(g->cta);
-  void* dptrs[] = {g->d_row_ptr, g->d_col_idx, g->d_w, g->d_v, g->d_vlo, g->d_ylo, g->d_perm, g->d_iperm, g->d_part,
+  void* dptrs[] = {g->d_row_ptr, g->d_col_idx, g->d_w, g->d_v, g->d_vlo, g->d_ylo, g->d_yexp, g->d_perm, g->d_iperm, g->d_part,
                    g->d_y[0], g->d_y[1], g->d_x, g->d_tmp, g->d_bsum, g->d_io, g->d_partials, g->d_bar, g->d_iterflag, g->d_inbox, g->d_info,
                    g->d_flags, g->d_red, g->d_mask, g->d_mask_c, g->d_bcount, g->d_bws,
                    g->d_members, g->d_hoff, g->d_hblob, g->d_gtab, g->d_cta_off};
@@ -400,6 +400,7 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
         {(void**)&g->d_v, nb},
         {(void**)&g->d_vlo, nb},
         {(void**)&g->d_ylo, nb},
+        {(void**)&g->d_yexp, nb},
         {(void**)&g->d_y[0], nb},
         {(void**)&g->d_y[1], nb},
         {(void**)&g->d_x, nb},

@@ -185,27 +185,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     for (int t = tid; t < nbytes / 16; t += blockDim.x) dst[t] = src[t];
   }
   // own rows: registers (REG) or shared memory
-  dev::f2 ry[2], rv[2];
-  float rx[2], rw[2];
+  Own ro[2];
+  dev::f2 rv[2];
+  float rw[2];
   if (REG) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int i = tid + j * kThreads;
       const bool in = i < nr;
       // a row past the CTA's end is a fixed point y = x = 1 (never a safe division)
-      ry[j] = in ? dev::f2{P.y0[rb + i], P.ylo[rb + i]} : dev::f2{1.0f, 0.0f};
+      ro[j] = in ? own_load(P.y0[rb + i], P.ylo[rb + i], P.x[rb + i], P.yexp[rb + i]) : Own{1.0f, 0.0f, 1.0f};
       rv[j] = in ? dev::f2{P.v[rb + i], P.vlo[rb + i]} : dev::f2{1.0f, 0.0f};
-      rx[j] = in ? P.x[rb + i] : 0.0f;
       rw[j] = in ? P.w[rb + i] : 0.0f;
-      if (in) S.yh[i] = ry[j].hi;
+      if (in) S.yh[i] = ro[j].pub;
     }
   } else {
     for (int i = tid; i < nr; i += blockDim.x) {
       S.vh[i] = P.v[rb + i];
       S.vl[i] = P.vlo[rb + i];
-      S.yh[i] = P.y0[rb + i];
-      S.yl[i] = P.ylo[rb + i];
-      S.x[i] = P.x[rb + i];
+      const Own o = own_load(P.y0[rb + i], P.ylo[rb + i], P.x[rb + i], P.yexp[rb + i]);
+      S.yh[i] = o.pub;
+      S.yl[i] = o.aux;
+      S.x[i] = o.xs;
     }
   }
   if (tid == 0) mbar_init(&s_bar, 1);
@@ -321,26 +322,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       const bool in0 = tid < nr, in1 = tid + kThreads < nr;
       RowStep s0;
       if (__any_sync(0xffffffffu, in1)) {
-        s0 = update_core(ry[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
-        const RowStep s1 = update_core(ry[1], rv[1], in1 ? S.sum[tid + kThreads] : 0.0f, gam);
-        if (check && in1) check_terms(s1, ry[1], rv[1], rx[1], rw[1], th_lo, th_hi, acc);
+        s0 = update_core(ro[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
+        const RowStep s1 = update_core(ro[1], rv[1], in1 ? S.sum[tid + kThreads] : 0.0f, gam);
+        if (check && in1) check_terms(s1, ro[1], rv[1], rw[1], th_lo, th_hi, acc);
         hits += in1 && !s1.ok ? 1ull : 0ull;
-        ry[1] = s1.yn;
-        rx[1] = s1.xn.hi;
+        ro[1] = s1.next;
         if (in1) {
-          s_all[tid + kThreads] = ry[1].hi;
-          if (!PUSH) yout[rb + tid + kThreads] = ry[1].hi;
+          s_all[tid + kThreads] = ro[1].pub;
+          if (!PUSH) yout[rb + tid + kThreads] = ro[1].pub;
         }
       } else {
-        s0 = update_core(ry[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
+        s0 = update_core(ro[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
       }
-      if (check && in0) check_terms(s0, ry[0], rv[0], rx[0], rw[0], th_lo, th_hi, acc);
+      if (check && in0) check_terms(s0, ro[0], rv[0], rw[0], th_lo, th_hi, acc);
       hits += in0 && !s0.ok ? 1ull : 0ull;
-      ry[0] = s0.yn;
-      rx[0] = s0.xn.hi;
+      ro[0] = s0.next;
       if (in0) {
-        s_all[tid] = ry[0].hi;
-        if (!PUSH) yout[rb + tid] = ry[0].hi;
+        s_all[tid] = ro[0].pub;
+        if (!PUSH) yout[rb + tid] = ro[0].pub;
       }
     } else {
       update_rows(S, nr, rb, P.w, PUSH ? nullptr : yout, gam, check, th_lo, th_hi, hits, acc);
@@ -379,9 +378,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     for (int j = 0; j < 2; ++j) {
       const int i = tid + j * kThreads;
       if (i < nr) {
-        S.x[i] = rx[j];
-        S.yl[i] = ry[j].lo;
-        yfin[rb + i] = ry[j].hi;
+        S.x[i] = ro[j].xs;
+        S.yl[i] = ro[j].aux;
+        S.vh[i] = rv[j].hi;  // own_x reads it
+        yfin[rb + i] = ro[j].pub;
       }
     }
     __syncthreads();

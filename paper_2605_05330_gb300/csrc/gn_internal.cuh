@@ -85,7 +85,8 @@ struct gn_graph {
   // state and scratch (device)
   float* d_y[2] = {nullptr, nullptr};
   float* d_x = nullptr;         // last returned state (internal order, clamped)
-  float* d_ylo = nullptr;       // low parts of the vertices' own weighted states after a run
+  float* d_ylo = nullptr;       // second words of the vertices' own states after a run (gn::Own::aux)
+  float* d_yexp = nullptr;      // their exponents (gn::Own::xs of a scaled state, else 0)
   int state_parity = 0;         // d_y[state_parity] holds the high parts of that state
   float* d_io = nullptr;        // staging for x0 / outputs (caller order)
   float* d_tmp = nullptr;       // internal-order scratch state

@@ -18,7 +18,8 @@ struct IterParams {
   float* y0;            // holds y^{k_start}
   float* y1;
   float* x;             // holds x^{k_start}; receives the final x (internal order)
-  float* ylo;           // low parts of the own weighted states (in and out)
+  float* ylo;           // Own::aux of every row (in and out)
+  float* yexp;          // Own::xs of the rows whose state is scaled, else 0 (in and out)
   CheckPartial* partials;
   unsigned* bar;
   int* status;
@@ -58,12 +59,13 @@ struct IterParams {
 static constexpr int kThreads = 1024;
 static constexpr float kSafeDiv = 1e-9f;
 
-// per-CTA shared arrays of the owned rows
+// per-CTA shared arrays of the owned rows (each row's own state is the triple (yh, yl, x),
+// see Own)
 struct RowArrays {
   float* sum;   // neighbour sums s_i of this iteration
-  float* yh;    // own weighted state, float pair
-  float* yl;
-  float* x;     // own x (FP32: residual and output)
+  float* yh;    // Own::pub
+  float* yl;    // Own::aux
+  float* x;     // Own::xs
   float* vh;    // v = sqrt(w), float pair
   float* vl;
 };
@@ -75,52 +77,99 @@ struct CheckAcc {
   float l1 = 0.0f, obj = 0.0f, en = 0.0f;
 };
 
+// The own state of a row, three words with an exponent range beyond FP32's.  Non-members decay
+// geometrically (App. G: by 1 / (gamma sum_{j in N(i) cap M} v_j / v_i) per step), so after a few
+// hundred steps many are far below FP32's smallest normal 2^-126.  Whether such a vertex comes
+// back later -- its neighbours decaying faster than it does, until x_i / d_i grows -- depends on
+// how deep it is, which FP32 would lose by storing 0.  The own state therefore carries its own
+// binary exponent; the value neighbours gather stays FP32, since a term below 2^-126 cannot move
+// a sum d_i = (B y)_i that is above the 1e-9 of the safe division.
+//   xs >= 0: y = pub + aux (float pair), x = xs;
+//   xs <  0: x < 2^-64, taken as 0 by the stop test; y = aux * 2^xs (xs a negative multiple of 64,
+//            aux the FP32 mantissa); pub = y rounded to FP32 (subnormal or 0 far down).
+// pub is the value the neighbours gather in both cases.
+struct Own {
+  float pub, aux, xs;
+};
+__device__ __forceinline__ bool own_scaled(const Own& s) { return s.xs < 0.0f; }
+// 2^e for e in {0, -64, -128, ...} as an FP32 value: 1, 2^-64, 2^-128 (subnormal), 0 below
+__device__ __forceinline__ float pow2_scale(float e) {
+  return e == 0.0f ? 1.0f : (e == -64.0f ? __int_as_float(0x1f800000) : (e == -128.0f ? __int_as_float(0x00200000) : 0.0f));
+}
+// the x of an own state as an FP32 value (the run's output): x = y / v
+__device__ __forceinline__ float own_x(const Own& s, float vh) {
+  return own_scaled(s) ? __fdiv_rn(s.aux, vh) * pow2_scale(s.xs) : s.xs;
+}
+// the own state of a run's start or of a saved state: pub / aux / x as stored, xe the saved
+// exponent (0 unless the state was scaled)
+__device__ __forceinline__ Own own_load(float pub, float aux, float x, float xe) {
+  return xe < 0.0f ? Own{pub, aux, xe} : Own{pub, aux, x};
+}
+
 // The update of one row (global id rb + i), arithmetic only:
 //   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. 3, WRGN, in the weighted state of Sec. 3 / App. B)
 //   d <= 1e-9: x' = 1/2 (the safe division of the appendix module)
-// Straight-line code (the safe division is a select), so a thread's rows can interleave.
+// The quotient is taken on the mantissa of y (y = m 2^e), so x' = (m / d) 2^e has the range of
+// the own state; after the step the mantissa is rescaled by 2^64 when x' leaves [2^-64, 1]
+// with e < 0 or drops below 2^-64.  For rows that never go below 2^-64 this is exactly the
+// float-pair update.  Straight-line code (the safe division is a select), so a thread's rows
+// can interleave.
 struct RowStep {
-  dev::f2 xn, yn;  // new x and y
+  Own next;        // the new own state
+  float x;         // x' as an FP32 value
+  float yin;       // y before the step as an FP32 value (the energy term)
   float d;         // (B y)_i, hi part (the energy term)
   bool ok;         // false: the safe division fired
 };
-__device__ __forceinline__ RowStep update_core(const dev::f2 y, const dev::f2 v, float sn, dev::f2 gam) {
+__device__ __forceinline__ RowStep update_core(const Own s, const dev::f2 v, float sn, dev::f2 gam) {
+  const bool sc = own_scaled(s);
+  const float e = sc ? s.xs : 0.0f;
+  const dev::f2 m = sc ? dev::f2{s.aux, 0.0f} : dev::f2{s.pub, s.aux};  // y = m 2^e
+  const dev::f2 y = sc ? dev::f2{s.pub, 0.0f} : m;                      // y in FP32 range
   dev::f2 p = dev::two_prod(gam.hi, sn);
   p.lo = dev::ffma(gam.lo, sn, p.lo);
   dev::f2 d = dev::two_sum(y.hi, p.hi);
   d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(y.lo, p.lo)));
   RowStep r;
   r.ok = d.hi > kSafeDiv;
-  const dev::f2 q = dev::div_f2(y, r.ok ? d : dev::f2{1.0f, 0.0f});
-  r.xn = r.ok ? q : dev::f2{0.5f, 0.0f};
-  r.yn = dev::mul_f2(v, r.xn);
+  const dev::f2 q = dev::div_f2(m, r.ok ? d : dev::f2{1.0f, 0.0f});
+  const dev::f2 xm = r.ok ? q : dev::f2{0.5f, 0.0f};  // x' = xm 2^ex
+  const float ex = r.ok ? e : 0.0f;
+  dev::f2 ym = dev::mul_f2(v, xm);                    // y' = ym 2^ex
+  const bool down = xm.hi < 0x1p-64f && xm.hi > 0.0f;
+  const bool up = ex < 0.0f && xm.hi >= 1.0f;
+  const float f = down ? 0x1p64f : (up ? 0x1p-64f : 1.0f);
+  const float en = ex + (down ? -64.0f : (up ? 64.0f : 0.0f));
+  ym.hi = dev::fmul(ym.hi, f);
+  ym.lo = dev::fmul(ym.lo, f);
+  r.x = dev::fmul(xm.hi, pow2_scale(ex));
+  r.next = en < 0.0f ? Own{dev::fmul(ym.hi, pow2_scale(en)), ym.hi, en} : Own{ym.hi, ym.lo, r.x};
+  r.yin = y.hi;
   r.d = d.hi;
   return r;
 }
-// a row's terms of the stop test (FP32 terms, summed as float pairs later): y, v and x are
-// the values before the step
-__device__ __forceinline__ void check_terms(const RowStep& r, const dev::f2 y, const dev::f2 v, float x, float wi,
+// a row's terms of the stop test (FP32 terms, summed as float pairs later): s, v are the state
+// and v before the step
+__device__ __forceinline__ void check_terms(const RowStep& r, const Own& s, const dev::f2 v, float wi,
                                             float th_lo, float th_hi, CheckAcc& acc) {
-  const float dx = fabsf(r.xn.hi - x);
+  const float dx = fabsf(r.x - (own_scaled(s) ? 0.0f : s.xs));
   acc.rmax = fmaxf(acc.rmax, dx);
   acc.l1 += dx;
-  acc.obj = __fmaf_rn(wi, r.xn.hi, acc.obj);
-  acc.en = __fmaf_rn(y.hi, __fmaf_rn(0.5f, r.d, -v.hi), acc.en);
-  acc.nonbin += (r.xn.hi > th_lo && r.xn.hi < th_hi) ? 1u : 0u;
+  acc.obj = __fmaf_rn(wi, r.x, acc.obj);
+  acc.en = __fmaf_rn(r.yin, __fmaf_rn(0.5f, r.d, -v.hi), acc.en);
+  acc.nonbin += (r.x > th_lo && r.x < th_hi) ? 1u : 0u;
 }
 // the update of one row with, at a check, its stop-test terms
-__device__ __forceinline__ void update_one(dev::f2& y, const dev::f2 v, float& x, float sn, dev::f2 gam,
-                                           bool check, float wi, float th_lo, float th_hi,
-                                           unsigned long long& hits, CheckAcc& acc) {
-  const RowStep r = update_core(y, v, sn, gam);
+__device__ __forceinline__ void update_one(Own& s, const dev::f2 v, float sn, dev::f2 gam, bool check, float wi,
+                                           float th_lo, float th_hi, unsigned long long& hits, CheckAcc& acc) {
+  const RowStep r = update_core(s, v, sn, gam);
   hits += r.ok ? 0ull : 1ull;
-  if (check) check_terms(r, y, v, x, wi, th_lo, th_hi, acc);
-  y = r.yn;
-  x = r.xn.hi;
+  if (check) check_terms(r, s, v, wi, th_lo, th_hi, acc);
+  s = r.next;
 }
 
 // the update of rows [0, nr) of the CTA with their state in shared memory (and, unless yout is
-// null, the new states to global memory)
+// null, the new gathered values to global memory)
 __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, const float* __restrict__ w,
                                             float* __restrict__ yout, dev::f2 gam, bool check,
                                             float th_lo, float th_hi, unsigned long long& hits,
@@ -131,26 +180,26 @@ __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, 
   for (int i = threadIdx.x; i < nr; i += 2 * step) {
     const int i2 = i + step;
     const bool in2 = i2 < nr;
-    const dev::f2 y1 = {S.yh[i], S.yl[i]};
-    const dev::f2 y2 = in2 ? dev::f2{S.yh[i2], S.yl[i2]} : dev::f2{1.0f, 0.0f};
+    const Own s1 = {S.yh[i], S.yl[i], S.x[i]};
+    const Own s2 = in2 ? Own{S.yh[i2], S.yl[i2], S.x[i2]} : Own{1.0f, 0.0f, 1.0f};
     const dev::f2 v1 = {S.vh[i], S.vl[i]};
     const dev::f2 v2 = in2 ? dev::f2{S.vh[i2], S.vl[i2]} : dev::f2{1.0f, 0.0f};
-    const RowStep r1 = update_core(y1, v1, S.sum[i], gam);
-    const RowStep r2 = update_core(y2, v2, in2 ? S.sum[i2] : 0.0f, gam);
+    const RowStep r1 = update_core(s1, v1, S.sum[i], gam);
+    const RowStep r2 = update_core(s2, v2, in2 ? S.sum[i2] : 0.0f, gam);
     if (check) {
-      check_terms(r1, y1, v1, S.x[i], w[rb + i], th_lo, th_hi, acc);
-      if (in2) check_terms(r2, y2, v2, S.x[i2], w[rb + i2], th_lo, th_hi, acc);
+      check_terms(r1, s1, v1, w[rb + i], th_lo, th_hi, acc);
+      if (in2) check_terms(r2, s2, v2, w[rb + i2], th_lo, th_hi, acc);
     }
     hits += (r1.ok ? 0ull : 1ull) + (in2 && !r2.ok ? 1ull : 0ull);
-    S.yh[i] = r1.yn.hi;
-    S.yl[i] = r1.yn.lo;
-    S.x[i] = r1.xn.hi;
-    if (yout) yout[rb + i] = r1.yn.hi;
+    S.yh[i] = r1.next.pub;
+    S.yl[i] = r1.next.aux;
+    S.x[i] = r1.next.xs;
+    if (yout) yout[rb + i] = r1.next.pub;
     if (in2) {
-      S.yh[i2] = r2.yn.hi;
-      S.yl[i2] = r2.yn.lo;
-      S.x[i2] = r2.xn.hi;
-      if (yout) yout[rb + i2] = r2.yn.hi;
+      S.yh[i2] = r2.next.pub;
+      S.yl[i2] = r2.next.aux;
+      S.x[i2] = r2.next.xs;
+      if (yout) yout[rb + i2] = r2.next.pub;
     }
   }
 }
@@ -414,14 +463,17 @@ __device__ __forceinline__ void set_gamma(const IterParams& P, int k, TailShared
   gamma_store(gamma_fetch(P, k), T);
 }
 
-// end of a run: own x and float-pair low parts back to global memory, safe-division count,
+// end of a run: own x, the second word of each own state and its exponent back to global memory
+// (the gathered values are already there), safe-division count,
 // iteration count and the parity of the buffer holding the final weighted state
 __device__ __forceinline__ void finish_run(const IterParams& P, const RowArrays& S, int rb, int nr,
                                            unsigned long long hits, int k, int parity, TailShared& T) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   for (int i = tid; i < nr; i += blockDim.x) {
-    P.x[rb + i] = S.x[i];
-    P.ylo[rb + i] = S.yl[i];
+    const Own s = {S.yh[i], S.yl[i], S.x[i]};
+    P.x[rb + i] = own_x(s, S.vh[i]);
+    P.ylo[rb + i] = s.aux;
+    P.yexp[rb + i] = own_scaled(s) ? s.xs : 0.0f;
   }
   unsigned long long h = dev::warp_sum_ull(hits);
   if (lane == 0) T.rh[warp] = h;

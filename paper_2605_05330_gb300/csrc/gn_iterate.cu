@@ -66,9 +66,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   for (int i = tid; i < nr; i += blockDim.x) {
     S.vh[i] = P.v[rb + i];
     S.vl[i] = P.vlo[rb + i];
-    S.yh[i] = P.y0[rb + i];
-    S.yl[i] = P.ylo[rb + i];
-    S.x[i] = P.x[rb + i];
+    const Own o = own_load(P.y0[rb + i], P.ylo[rb + i], P.x[rb + i], P.yexp[rb + i]);
+    S.yh[i] = o.pub;
+    S.yl[i] = o.aux;
+    S.x[i] = o.xs;
   }
   __syncthreads();
   if (SMEM_CSR) {
@@ -157,7 +158,7 @@ __global__ void k_init_state(int n, const int32_t* __restrict__ rp, const int32_
                              const float* __restrict__ v, const float* __restrict__ vlo,
                              const float* __restrict__ x0, const int32_t* __restrict__ perm,
                              float* __restrict__ x, float* __restrict__ y, float* __restrict__ ylo,
-                             int* status) {
+                             float* __restrict__ yexp, int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int b = rp[i], e = rp[i + 1];
@@ -179,6 +180,7 @@ __global__ void k_init_state(int n, const int32_t* __restrict__ rp, const int32_
   dev::f2 yy = dev::mul_f2(dev::f2{v[i], vlo[i]}, dev::f2{xi, 0.0f});
   y[i] = yy.hi;
   ylo[i] = yy.lo;
+  yexp[i] = 0.0f;
 }
 
 __global__ void k_to_caller(int n, const float* __restrict__ x_int, const int32_t* __restrict__ iperm,
@@ -325,7 +327,8 @@ gn_status init_state(gn_graph* g, const float* x0_dev) {
   if (g->n == 0) return GN_OK;
   k_init_state<<<(g->n + 255) / 256, 256, 0, g->stream>>>(g->n, g->d_row_ptr, g->d_col_idx, g->d_v,
                                                            g->d_vlo, x0_dev, g->d_perm, g->d_x,
-                                                           g->d_y[0], g->d_ylo, &g->d_info->status);
+                                                           g->d_y[0], g->d_ylo, g->d_yexp,
+                                                           &g->d_info->status);
   g->state_parity = 0;
   GN_LAUNCHED();
   GN_CUDA(cudaGetLastError());
@@ -362,6 +365,7 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.y1 = g->d_y[parity0 ^ 1];
   P.x = g->d_x;
   P.ylo = g->d_ylo;
+  P.yexp = g->d_yexp;
   P.hoff = g->d_hoff;
   P.hblob = g->d_hblob;
   P.halo_pad = g->halo_pad;
@@ -602,7 +606,8 @@ static constexpr size_t kNaVec = align256(sizeof(float) * kNoAllocMaxN);
 static constexpr size_t kNaOffY0 = 0;
 static constexpr size_t kNaOffY1 = kNaOffY0 + kNaVec;
 static constexpr size_t kNaOffYlo = kNaOffY1 + kNaVec;
-static constexpr size_t kNaOffV = kNaOffYlo + kNaVec;
+static constexpr size_t kNaOffYexp = kNaOffYlo + kNaVec;
+static constexpr size_t kNaOffV = kNaOffYexp + kNaVec;
 static constexpr size_t kNaOffVlo = kNaOffV + kNaVec;
 static constexpr size_t kNaOffPartials = kNaOffVlo + kNaVec;
 static constexpr size_t kNaOffPart = kNaOffPartials + align256(sizeof(CheckPartial) * 2 * kNoAllocMaxCTAs);
@@ -612,16 +617,18 @@ static constexpr size_t kNaOffBar = kNaOffInfo + align256(sizeof(DevInfo));
 static constexpr size_t kNaOffGtab = kNaOffBar + 256;
 static constexpr size_t kNoAllocScratchBytes = kNaOffGtab + align256(sizeof(float2) * kNoAllocMaxGamma);
 
-// the fixed scratch (about 1.5 MB per device)
+// the fixed scratch (about 1.7 MB per device)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// range, order and self-loop check of the caller's CSR (flags go to the run summary's status)
-__global__ void k_na_check_rows(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+// range, order and self-loop check of the caller's CSR (flags go to the run summary's status).
+// nnz = row_ptr[n] as read on the host: a row whose range leaves [0, nnz) is malformed and its
+// entries are not read, so a row_ptr that decreases further on cannot send a row past col_idx.
+__global__ void k_na_check_rows(int n, int nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                 int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int b = rp[i], e = rp[i + 1];
-  if (b < 0 || e < b || (i == 0 && b != 0)) {
+  if (b < 0 || e < b || e > nnz || (i == 0 && b != 0)) {
     atomicOr(status, DEV_BAD_CSR);
     return;
   }
@@ -665,8 +672,8 @@ __global__ void k_na_check_symmetry(int n, const int32_t* __restrict__ rp, const
 __global__ void k_na_init(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                           const float* __restrict__ w, const float* __restrict__ x0, float* __restrict__ v,
                           float* __restrict__ vlo, float* __restrict__ x, float* __restrict__ y,
-                          float* __restrict__ ylo, int32_t* __restrict__ part, int nblocks, int rows_per,
-                          int* status) {
+                          float* __restrict__ ylo, float* __restrict__ yexp, int32_t* __restrict__ part,
+                          int nblocks, int rows_per, int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   // the partition is written first and unconditionally: the iteration kernel reads it
   // (and returns at once when the status word is set)
@@ -692,9 +699,12 @@ __global__ void k_na_init(int n, const int32_t* __restrict__ rp, const int32_t* 
   dev::f2 yy = dev::mul_f2(vv, dev::f2{xi, 0.0f});
   y[i] = yy.hi;
   ylo[i] = yy.lo;
+  yexp[i] = 0.0f;
 }
 
-__global__ void k_na_clamp(int n, float* __restrict__ x) {
+// the result clamped to [0, 1]; nothing is written when the run failed (the status word is set)
+__global__ void k_na_clamp(int n, float* __restrict__ x, const int* status) {
+  if (dev::ld_relaxed_int(status) != 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = fminf(fmaxf(x[i], 0.0f), 1.0f);
 }
@@ -746,6 +756,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
   float* s_y0 = reinterpret_cast<float*>(base + kNaOffY0);
   float* s_y1 = reinterpret_cast<float*>(base + kNaOffY1);
   float* s_ylo = reinterpret_cast<float*>(base + kNaOffYlo);
+  float* s_yexp = reinterpret_cast<float*>(base + kNaOffYexp);
   float* s_v = reinterpret_cast<float*>(base + kNaOffV);
   float* s_vlo = reinterpret_cast<float*>(base + kNaOffVlo);
   CheckPartial* s_partials = reinterpret_cast<CheckPartial*>(base + kNaOffPartials);
@@ -790,12 +801,12 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
   GN_CUDA(cudaMemsetAsync(s_info, 0, sizeof(DevInfo), stream));
   GN_CUDA(cudaMemsetAsync(s_bar, 0, sizeof(unsigned) * 8, stream));  // counter and check words
   const unsigned grid = (unsigned)std::max(n, nb + 1);
-  k_na_check_rows<<<(n + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, &s_info->status);
+  k_na_check_rows<<<(n + 255) / 256, 256, 0, stream>>>(n, nnz, row_ptr, col_idx, &s_info->status);
   GN_LAUNCHED();
   k_na_check_symmetry<<<(n + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, &s_info->status);
   GN_LAUNCHED();
   k_na_init<<<(grid + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, w, x0, s_v, s_vlo, x_out, s_y0,
-                                                     s_ylo, s_part, nb, rows_per, &s_info->status);
+                                                     s_ylo, s_yexp, s_part, nb, rows_per, &s_info->status);
   GN_LAUNCHED();
   GN_CUDA(cudaGetLastError());
 
@@ -814,6 +825,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     P.y1 = s_y1;
     P.x = x_out;
     P.ylo = s_ylo;
+    P.yexp = s_yexp;
     P.hoff = nullptr;
     P.hblob = nullptr;
     P.halo_pad = 0;
@@ -854,7 +866,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     GN_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(nb), dim3(kThreads), args, smem, stream));
     GN_LAUNCHED();
     if (timed) GN_CUDA(cudaEventRecord(e1, stream));
-    k_na_clamp<<<(n + 255) / 256, 256, 0, stream>>>(n, x_out);
+    k_na_clamp<<<(n + 255) / 256, 256, 0, stream>>>(n, x_out, &s_info->status);
     GN_LAUNCHED();
     GN_CUDA(cudaMemcpyAsync(&di, s_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, stream));
     GN_CUDA(cudaStreamSynchronize(stream));

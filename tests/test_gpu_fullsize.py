@@ -2,14 +2,15 @@
 unit-disk (n = 200,000, |E| ~ 1.0M) and Barabasi-Albert (n = 200,000, m = 5) graphs on the
 device-resident path.  Per-vertex iterate parity after a few steps, then the complete run to
 a binary state checked for exact independence and maximality, its FP64 objective and W(S)
-re-computed by the oracle, and the final set compared with the oracle's when the instance
-has no near-ties."""
+re-computed by the oracle, the safe-division hits and iteration count equal to the oracle's,
+and the final set equal to the oracle's when the instance has no near-ties (the unit-disk
+graph; the BA graph has near-ties)."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_2605_05330_gb300 import inputs
-from tests.test_gpu_parity import assert_close_rel, dev_graph, fixed_steps, to_np
+from tests.test_gpu_parity import _tie_free, assert_close_rel, dev_graph, fixed_steps, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -101,19 +102,22 @@ def test_fullsize_run_to_binary(gn, workload):
     np.testing.assert_array_equal(to_np(members), memo)
     assert cnt == len(memo) and abs(W - Wo) <= 1e-12 * Wo
     assert abs(info["objective"] - oracle.objective(inst.w, xh)) <= 1e-9 * Wo
-    # against the oracle's own FP64 run.  Non-members decay geometrically; FP32's exponent
-    # range (smallest normal 1.2e-38) stores a deeply decayed vertex as 0 where FP64 would let
-    # it recover later, and the paper's safe division re-admits it.  Emulating FP32's range in
-    # the FP64 iteration changes 2 of 200,000 final memberships on the unit-disk graph and none
-    # on the BA graph, so the bar here is agreement >= 99.99% and |objective gap| <= 1e-4.
+    # against the oracle's own FP64 run: the same safe-division hits and the same iteration
+    # count, and on an instance without near-ties (the oracle gives the same set from x0 and from
+    # x0 (1 +- 1e-3 u)) the same set bit for bit.  The own states carry an exponent beyond
+    # FP32's range, so deeply decayed non-members follow the FP64 run instead of stopping at 0.
     p = oracle.params(check_every=10)
     xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=2000, tol=1e-7, p=p)
     assert io["status"] == "OK"
     set_o = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)[1]
-    agree = np.mean(to_np(mask) == set_o)
+    differ = int(np.sum(to_np(mask) != set_o))
     gap = (io["objective"] - info["objective"]) / io["objective"]
-    print(f"{inst.name}: iters gpu={info['iters']} oracle={io['iters']} agree={agree:.6f} gap={gap:.2e} "
-          f"hits gpu={info['safe_div_hits']} oracle={io['safe_div_hits']}")
-    assert agree >= 0.9999 and abs(gap) <= 1e-4
-    if info["safe_div_hits"] == 0 and io["safe_div_hits"] == 0:
+    tie_free = _tie_free(inst, p)
+    print(f"{inst.name}: iters gpu={info['iters']} oracle={io['iters']} differ={differ} gap={gap:.2e} "
+          f"hits gpu={info['safe_div_hits']} oracle={io['safe_div_hits']} tie_free={tie_free}")
+    assert info["safe_div_hits"] == io["safe_div_hits"]
+    assert info["iters"] == io["iters"]
+    if tie_free:
         np.testing.assert_array_equal(to_np(mask), set_o)
+    # which of the two graphs are tie-free is a property of the inputs, fixed by the oracle
+    assert tie_free == (inst.meta["kind"] == "udg")
