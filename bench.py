@@ -708,7 +708,8 @@ def main():
                        "reorder": {"udg": "rcm", "ba": "none"},
                        "graphs": per_graph, "max_iters": MAX_ITERS, "tol": TOL, "check_every": CHECK_EVERY,
                        "gamma": "pursuit 0.9->1.5 over 1000", "l2": "flushed between timed steps (256 MB write)",
-                       "reductions": "fp64"},
+                       "reductions": "FP32 per-row terms accumulated in float pairs (about 2^-44 relative per "
+                                     "addition), one FP64 rounding per total"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(),
                          "kernel": "k_gn_halo", "peak_kind": peak_kind,

@@ -257,22 +257,29 @@ gn_status gn_backward(gn_graph* g, const float* dL_dxT, float* dL_dw, float* dL_
  * themselves (a plugin inside another framework's memory pool, a service that allocates
  * everything at start-up, work issued while the allocator is locked).  This entry point
  * allocates nothing: no cudaMalloc, no cudaFree, no handle.  All of the kernel's scratch
- * (weighted states, v = sqrt(w) as a float pair, per-CTA check partials, the grid-barrier
- * counter, the run summary, the gamma schedule) lives in one fixed array of about 1.5 MB in
+ * (the working states, v = sqrt(w) as a float pair, per-CTA check partials, the grid-barrier
+ * counter, the run summary, the gamma schedule) lives in one fixed array of about 2 MB in
  * the library's device globals, which every GPU that loads the library holds until the
  * process exits.  The gamma pursuit may span at most 16384 table entries.
  *   n, row_ptr, col_idx, w   the graph, DEVICE pointers, same layout and rules as gn_create;
- *                            n <= 65536 (GN_ERR_TOO_LARGE beyond); the CSR is validated on the
- *                            device (range, order, self-loops, symmetry, weights)
+ *                            n <= 65536 (GN_ERR_TOO_LARGE beyond); row_ptr[n] is read on the
+ *                            host, then the CSR is validated on the device (every row's range
+ *                            within [0, row_ptr[n]] before its entries are read, order,
+ *                            self-loops, symmetry, weights)
  *   x0, max_iters, tol, p, start_iter, info   as gn_run (DEVICE x0 or NULL); p->resume is
  *                            not available (GN_ERR_ARG)
- *   x_out                    float32[n] DEVICE output, also used as the working x
+ *   x_out                    float32[n] DEVICE output, written only when the call succeeds
+ *                            (GN_OK or a warning); an error leaves it untouched
  *   stream                   cudaStream_t for all the work (NULL = default stream)
- * Results equal gn_run's for the same inputs.  Calls share the fixed array and leave their
- * contents in it: calls whose device work overlaps (several host threads or streams) race and
- * must be serialised by the caller.  The first call on each device resolves the array's
- * address with cudaGetSymbolAddress and sets a kernel attribute; make it before any stream
- * capture.  Returns the same codes as gn_run, plus GN_ERR_ARG / GN_ERR_NOT_SIMPLE /
+ * Results equal those of gn_run on a handle made with GN_GATHER_GLOBAL and GN_REORDER_NONE
+ * (the same kernel and per-row summation order; only the split of rows over CTAs differs);
+ * against gn_run's default (halo gather, RCM order) they agree within the per-vertex parity
+ * tolerance.  Calls share the fixed array and leave their contents in it: calls whose device
+ * work overlaps (several host threads or streams) race and must be serialised by the caller.
+ * Every call reads row_ptr[n] and the run summary back to the host and synchronises the
+ * stream, so it cannot be made while the stream is being captured into a CUDA graph.  The
+ * first call on each device resolves the array's address with cudaGetSymbolAddress and sets a
+ * kernel attribute.  Returns the same codes as gn_run, plus GN_ERR_ARG / GN_ERR_NOT_SIMPLE /
  * GN_ERR_WEIGHT for a bad graph.
  */
 gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const float* w,

@@ -86,7 +86,7 @@ struct CheckAcc {
 // a sum d_i = (B y)_i that is above the 1e-9 of the safe division.
 //   xs >= 0: y = pub + aux (float pair), x = xs;
 //   xs <  0: x < 2^-64, taken as 0 by the stop test; y = aux * 2^xs (xs a negative multiple of 64,
-//            aux the FP32 mantissa); pub = y rounded to FP32 (subnormal or 0 far down).
+//            aux the FP32 mantissa); pub = y in FP32 at xs = -64, 0 further down.
 // pub is the value the neighbours gather in both cases.
 struct Own {
   float pub, aux, xs;
@@ -110,41 +110,45 @@ __device__ __forceinline__ Own own_load(float pub, float aux, float x, float xe)
 //   d = y + gamma s = (B y)_i, x' = y / d, y' = v x'  (Def. 3, WRGN, in the weighted state of Sec. 3 / App. B)
 //   d <= 1e-9: x' = 1/2 (the safe division of the appendix module)
 // The quotient is taken on the mantissa of y (y = m 2^e), so x' = (m / d) 2^e has the range of
-// the own state; after the step the mantissa is rescaled by 2^64 when x' leaves [2^-64, 1]
-// with e < 0 or drops below 2^-64.  For rows that never go below 2^-64 this is exactly the
-// float-pair update.  Straight-line code (the safe division is a select), so a thread's rows
-// can interleave.
+// the own state; after the step the mantissa is rescaled by 2^64 when x' drops below 2^-64, or
+// when it is back at or above 2^-64 with e < 0.  For rows that never go below 2^-64 this is
+// exactly the float-pair update.  A scaled row's x is taken as 0 in the stop test and in the
+// objective (it is below 2^-64), and its gathered value is exact at e = -64 and 0 further down
+// (below 2^-104 v, nothing next to a sum above the safe-division threshold).  Straight-line
+// code (the safe division is a select), so a thread's rows can interleave.
 struct RowStep {
   Own next;        // the new own state
-  float x;         // x' as an FP32 value
+  float x;         // x' as an FP32 value (0 for a scaled row)
   float yin;       // y before the step as an FP32 value (the energy term)
   float d;         // (B y)_i, hi part (the energy term)
   bool ok;         // false: the safe division fired
 };
 __device__ __forceinline__ RowStep update_core(const Own s, const dev::f2 v, float sn, dev::f2 gam) {
   const bool sc = own_scaled(s);
-  const float e = sc ? s.xs : 0.0f;
-  const dev::f2 m = sc ? dev::f2{s.aux, 0.0f} : dev::f2{s.pub, s.aux};  // y = m 2^e
-  const dev::f2 y = sc ? dev::f2{s.pub, 0.0f} : m;                      // y in FP32 range
+  const float e = fminf(s.xs, 0.0f);
+  const float mh = sc ? s.aux : s.pub, ml = sc ? 0.0f : s.aux;  // y = (mh + ml) 2^e
   dev::f2 p = dev::two_prod(gam.hi, sn);
   p.lo = dev::ffma(gam.lo, sn, p.lo);
-  dev::f2 d = dev::two_sum(y.hi, p.hi);
-  d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(y.lo, p.lo)));
+  dev::f2 d = dev::two_sum(s.pub, p.hi);                         // y in FP32 range: (pub, ml)
+  d = dev::fast_two_sum(d.hi, dev::fadd(d.lo, dev::fadd(ml, p.lo)));
   RowStep r;
   r.ok = d.hi > kSafeDiv;
-  const dev::f2 q = dev::div_f2(m, r.ok ? d : dev::f2{1.0f, 0.0f});
-  const dev::f2 xm = r.ok ? q : dev::f2{0.5f, 0.0f};  // x' = xm 2^ex
+  const dev::f2 q = dev::div_f2(dev::f2{mh, ml}, r.ok ? d : dev::f2{1.0f, 0.0f});
+  const dev::f2 xm = r.ok ? q : dev::f2{0.5f, 0.0f};            // x' = xm 2^ex
   const float ex = r.ok ? e : 0.0f;
-  dev::f2 ym = dev::mul_f2(v, xm);                    // y' = ym 2^ex
+  dev::f2 ym = dev::mul_f2(v, xm);                                // y' = ym 2^ex
   const bool down = xm.hi < 0x1p-64f && xm.hi > 0.0f;
-  const bool up = ex < 0.0f && xm.hi >= 1.0f;
+  const bool neg = ex < 0.0f;
+  const bool up = neg && xm.hi >= 1.0f;
   const float f = down ? 0x1p64f : (up ? 0x1p-64f : 1.0f);
   const float en = ex + (down ? -64.0f : (up ? 64.0f : 0.0f));
   ym.hi = dev::fmul(ym.hi, f);
   ym.lo = dev::fmul(ym.lo, f);
-  r.x = dev::fmul(xm.hi, pow2_scale(ex));
-  r.next = en < 0.0f ? Own{dev::fmul(ym.hi, pow2_scale(en)), ym.hi, en} : Own{ym.hi, ym.lo, r.x};
-  r.yin = y.hi;
+  r.x = neg ? 0.0f : xm.hi;
+  const bool nsc = en < 0.0f;
+  const float sp = en == -64.0f ? 0x1p-64f : 0.0f;
+  r.next = Own{nsc ? dev::fmul(ym.hi, sp) : ym.hi, nsc ? ym.hi : ym.lo, nsc ? en : r.x};
+  r.yin = s.pub;
   r.d = d.hi;
   return r;
 }

@@ -595,8 +595,9 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
 //     whose device work overlaps (two host threads, or two streams) race and corrupt each
 //     other: serialise them;
 //   - the first call on each device resolves the array's device address with
-//     cudaGetSymbolAddress (and sets the kernel's shared-memory attribute), so make that first
-//     call before any stream capture begins.
+//     cudaGetSymbolAddress (and sets the kernel's shared-memory attribute);
+//   - every call reads row_ptr[n] and the run summary back to the host and synchronises the
+//     stream, so no call may be made while the stream is being captured.
 namespace gn {
 
 static constexpr int kNoAllocMaxN = 65536;
@@ -607,7 +608,8 @@ static constexpr size_t kNaOffY0 = 0;
 static constexpr size_t kNaOffY1 = kNaOffY0 + kNaVec;
 static constexpr size_t kNaOffYlo = kNaOffY1 + kNaVec;
 static constexpr size_t kNaOffYexp = kNaOffYlo + kNaVec;
-static constexpr size_t kNaOffV = kNaOffYexp + kNaVec;
+static constexpr size_t kNaOffX = kNaOffYexp + kNaVec;
+static constexpr size_t kNaOffV = kNaOffX + kNaVec;
 static constexpr size_t kNaOffVlo = kNaOffV + kNaVec;
 static constexpr size_t kNaOffPartials = kNaOffVlo + kNaVec;
 static constexpr size_t kNaOffPart = kNaOffPartials + align256(sizeof(CheckPartial) * 2 * kNoAllocMaxCTAs);
@@ -617,7 +619,7 @@ static constexpr size_t kNaOffBar = kNaOffInfo + align256(sizeof(DevInfo));
 static constexpr size_t kNaOffGtab = kNaOffBar + 256;
 static constexpr size_t kNoAllocScratchBytes = kNaOffGtab + align256(sizeof(float2) * kNoAllocMaxGamma);
 
-// the fixed scratch (about 1.7 MB per device)
+// the fixed scratch (about 2 MB per device)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // range, order and self-loop check of the caller's CSR (flags go to the run summary's status).
@@ -702,11 +704,12 @@ __global__ void k_na_init(int n, const int32_t* __restrict__ rp, const int32_t* 
   yexp[i] = 0.0f;
 }
 
-// the result clamped to [0, 1]; nothing is written when the run failed (the status word is set)
-__global__ void k_na_clamp(int n, float* __restrict__ x, const int* status) {
+// the result, clamped to [0, 1], into the caller's buffer; nothing is written when the run
+// failed (the status word is set)
+__global__ void k_na_out(int n, const float* __restrict__ x, float* __restrict__ out, const int* status) {
   if (dev::ld_relaxed_int(status) != 0) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = fminf(fmaxf(x[i], 0.0f), 1.0f);
+  if (i < n) out[i] = fminf(fmaxf(x[i], 0.0f), 1.0f);
 }
 
 static std::mutex g_na_mutex;
@@ -757,6 +760,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
   float* s_y1 = reinterpret_cast<float*>(base + kNaOffY1);
   float* s_ylo = reinterpret_cast<float*>(base + kNaOffYlo);
   float* s_yexp = reinterpret_cast<float*>(base + kNaOffYexp);
+  float* s_x = reinterpret_cast<float*>(base + kNaOffX);
   float* s_v = reinterpret_cast<float*>(base + kNaOffV);
   float* s_vlo = reinterpret_cast<float*>(base + kNaOffVlo);
   CheckPartial* s_partials = reinterpret_cast<CheckPartial*>(base + kNaOffPartials);
@@ -805,7 +809,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
   GN_LAUNCHED();
   k_na_check_symmetry<<<(n + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, &s_info->status);
   GN_LAUNCHED();
-  k_na_init<<<(grid + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, w, x0, s_v, s_vlo, x_out, s_y0,
+  k_na_init<<<(grid + 255) / 256, 256, 0, stream>>>(n, row_ptr, col_idx, w, x0, s_v, s_vlo, s_x, s_y0,
                                                      s_ylo, s_yexp, s_part, nb, rows_per, &s_info->status);
   GN_LAUNCHED();
   GN_CUDA(cudaGetLastError());
@@ -823,7 +827,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     P.part = s_part;
     P.y0 = s_y0;
     P.y1 = s_y1;
-    P.x = x_out;
+    P.x = s_x;
     P.ylo = s_ylo;
     P.yexp = s_yexp;
     P.hoff = nullptr;
@@ -866,7 +870,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     GN_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3(nb), dim3(kThreads), args, smem, stream));
     GN_LAUNCHED();
     if (timed) GN_CUDA(cudaEventRecord(e1, stream));
-    k_na_clamp<<<(n + 255) / 256, 256, 0, stream>>>(n, x_out, &s_info->status);
+    k_na_out<<<(n + 255) / 256, 256, 0, stream>>>(n, s_x, x_out, &s_info->status);
     GN_LAUNCHED();
     GN_CUDA(cudaMemcpyAsync(&di, s_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, stream));
     GN_CUDA(cudaStreamSynchronize(stream));
@@ -876,6 +880,8 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
       cudaEventDestroy(e1);
     }
   } else {
+    k_na_out<<<(n + 255) / 256, 256, 0, stream>>>(n, s_x, x_out, &s_info->status);  // the start state
+    GN_LAUNCHED();
     GN_CUDA(cudaMemcpyAsync(&di, s_info, sizeof(DevInfo), cudaMemcpyDeviceToHost, stream));
     GN_CUDA(cudaStreamSynchronize(stream));
   }

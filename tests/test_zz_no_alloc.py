@@ -87,3 +87,91 @@ def test_noalloc_rejects_graphs_above_its_limit(env):
                           P(x.data_ptr()), None, None)
     assert gn.STATUS[st] == "ERR_TOO_LARGE"
     assert b"65536" in L.gn_last_error()
+
+
+def _call(torch, gn, L, n, rp, ci, w, x0, max_iters, tol, params, start_iter, x):
+    P = ctypes.c_void_p
+    info = gn.RunInfo()
+    st = L.gn_run_noalloc(n, P(rp.data_ptr()), P(ci.data_ptr()) if ci is not None else None, P(w.data_ptr()),
+                          P(x0.data_ptr()) if x0 is not None else None, max_iters, tol, ctypes.byref(params),
+                          start_iter, P(x.data_ptr()), ctypes.byref(info), None)
+    torch.cuda.synchronize()
+    return gn.STATUS[st], info
+
+
+def test_noalloc_start_state_and_resumed_runs(env):
+    """A caller's x0 (with a zero entry that a positive neighbour makes normalizable, Def. 1)
+    and a run that starts at start_iter > 0 from a saved FP32 state: both as gn_run on a
+    GN_GATHER_GLOBAL handle."""
+    torch, gn, L = env
+    inst = inputs.er_graph(4000, 8.0, 4331)
+    dev = torch.device("cuda", 0)
+    rp = torch.from_numpy(inst.row_ptr).to(dev)
+    ci = torch.from_numpy(inst.col_idx).to(dev)
+    w = torch.from_numpy(inst.w).to(dev)
+    x0 = torch.from_numpy(inputs.uniforms(inst.n, 4332)).to(dev)
+    x0[3] = 0.0
+    assert int(inst.row_ptr[4] - inst.row_ptr[3]) > 0
+    g = gn.Graph(rp, ci, w, gather=gn.GATHER_GLOBAL)
+    pk = gn.default_params(theta_bin=-1.0, check_every=1)
+    x = torch.empty(inst.n, dtype=torch.float32, device=dev)
+    st, info = _call(torch, gn, L, inst.n, rp, ci, w, x0, 20, -1.0, pk, 0, x)
+    xr, ir = g.run(x0=x0, max_iters=20, tol=-1.0, params=pk)
+    assert st == ir["status"] and info.iters == ir["iters"] == 20
+    xn, xrn = x.cpu().numpy().astype(np.float64), xr.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(xn - xrn) <= REL * np.maximum(np.abs(xrn), FLOOR))
+    # resume from the 300-step state at start_iter = 300, to a binary state
+    xs, _ = g.run(max_iters=300, tol=-1.0)
+    xs = xs.clone()
+    st, info = _call(torch, gn, L, inst.n, rp, ci, w, xs, 2000, 1e-7, gn.default_params(), 300, x)
+    xr, ir = g.run(x0=xs, max_iters=2000, start_iter=300)
+    assert st == ir["status"] == "OK" and info.iters == ir["iters"]
+    assert np.array_equal(x.cpu().numpy() > 0.5, xr.cpu().numpy() > 0.5)
+    g.close()
+
+
+def test_noalloc_rejects_bad_inputs_and_leaves_the_output(env):
+    """Weights that are not positive and finite (GN_ERR_WEIGHT), a CSR that is not simple
+    (asymmetric, or with a self-loop: GN_ERR_NOT_SIMPLE), a row_ptr that decreases further on
+    (GN_ERR_ARG, the rows are bounded by row_ptr[n] before their entries are read) and a wait
+    that times out (GN_ERR_TIMEOUT, through the test hook that makes the first grid barrier
+    unreachable): each returns its status, leaves x_out as it was, and the next call works."""
+    torch, gn, L = env
+    dev = torch.device("cuda", 0)
+    inst = inputs.er_graph(3000, 6.0, 4341)
+    rp = torch.from_numpy(inst.row_ptr).to(dev)
+    ci = torch.from_numpy(inst.col_idx).to(dev)
+    w = torch.from_numpy(inst.w).to(dev)
+    p = gn.default_params()
+    x = torch.full((inst.n,), 7.0, dtype=torch.float32, device=dev)
+
+    def untouched():
+        return bool(torch.all(x == 7.0).item())
+
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        wb = w.clone()
+        wb[5] = bad
+        st, _ = _call(torch, gn, L, inst.n, rp, ci, wb, None, 100, 1e-7, p, 0, x)
+        assert st == "ERR_WEIGHT" and untouched()
+    # asymmetric: drop one direction of an edge; self-loop: a row that lists itself
+    tiny_rp = torch.tensor([0, 1, 1], dtype=torch.int32, device=dev)
+    tiny_ci = torch.tensor([1], dtype=torch.int32, device=dev)
+    tiny_w = torch.ones(2, dtype=torch.float32, device=dev)
+    x2 = torch.full((2,), 7.0, dtype=torch.float32, device=dev)
+    st, _ = _call(torch, gn, L, 2, tiny_rp, tiny_ci, tiny_w, None, 10, 1e-7, p, 0, x2)
+    assert st == "ERR_NOT_SIMPLE" and bool(torch.all(x2 == 7.0).item())
+    loop_rp = torch.tensor([0, 1, 2], dtype=torch.int32, device=dev)
+    loop_ci = torch.tensor([0, 1], dtype=torch.int32, device=dev)
+    st, _ = _call(torch, gn, L, 2, loop_rp, loop_ci, tiny_w, None, 10, 1e-7, p, 0, x2)
+    assert st == "ERR_NOT_SIMPLE" and bool(torch.all(x2 == 7.0).item())
+    # row 0 claims [0, 2^30) although row_ptr[n] = 10 and col_idx holds 10 entries
+    dec_rp = torch.tensor([0, 1 << 30, 10], dtype=torch.int32, device=dev)
+    dec_ci = torch.ones(10, dtype=torch.int32, device=dev)
+    st, _ = _call(torch, gn, L, 2, dec_rp, dec_ci, tiny_w, None, 10, 1e-7, p, 0, x2)
+    assert st == "ERR_ARG" and bool(torch.all(x2 == 7.0).item())
+    # a barrier nothing can satisfy: bounded wait, status returned, context usable
+    pt = gn.default_params(debug_unreachable_barrier=1, spin_limit=2000)
+    st, _ = _call(torch, gn, L, inst.n, rp, ci, w, None, 100, 1e-7, pt, 0, x)
+    assert st == "ERR_TIMEOUT" and untouched()
+    st, info = _call(torch, gn, L, inst.n, rp, ci, w, None, 2000, 1e-7, p, 0, x)
+    assert st == "OK" and info.iters > 0 and bool(torch.all((x >= 0) & (x <= 1)).item())
