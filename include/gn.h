@@ -164,6 +164,20 @@ void gn_destroy(gn_graph* g);
 /* Changes the memory side (GN_HOST / GN_DEVICE) of the pointers of later calls. */
 gn_status gn_set_io(gn_graph* g, int mem);
 
+/*
+ * gn_set_weights -- replaces the vertex weights w of Def. 3 (WRGN) on an existing handle, with
+ * v = sqrt(w) recomputed as a float pair, so that a caller who changes only the weights (the
+ * differentiable form's parameters, a sweep over weightings) pays neither validation of the
+ * CSR nor reordering nor the per-CTA block build again.
+ *   w   float32[n] in caller order, on the side of the handle's I/O mode; every entry must be
+ *       finite and > 0
+ * The handle's graph, vertex order and layout are unchanged.  Its recorded forward run (if
+ * any), its resumable state and its CTA-kernel copy of the instance are dropped: gn_backward
+ * then returns GN_ERR_NO_RECORD and a resume GN_ERR_ARG until the next run.  Errors:
+ * GN_ERR_ARG, GN_ERR_WEIGHT (the old weights stay in place), GN_ERR_CUDA.
+ */
+gn_status gn_set_weights(gn_graph* g, const float* w);
+
 /* Graph size queries. */
 int32_t gn_num_vertices(const gn_graph* g);
 int64_t gn_num_entries(const gn_graph* g);
@@ -340,8 +354,17 @@ float gn_batch_last_ms(gn_batch* b);
 /* CTA size of the batch kernel (128, 256, 512 or 1024). */
 gn_status gn_batch_set_threads(gn_batch* b, int threads);
 
-/* Autotuner: times the batch kernel at each CTA size for max_iters iterations (twice each) and
- * keeps the fastest; *threads_out receives it (may be NULL). */
+/* Instance packing: instances of at most warp_max_vertices vertices (0: none) that fit one warp's
+ * share of the CTA's shared memory run a warp each, several per CTA, once the CTA-per-instance
+ * queue is empty (same launch).  Iterates are bit-identical to CTA mode (same lanes per row, same
+ * summation order).  gn_batch_packing reports the threshold and how many instances it moves. */
+gn_status gn_batch_set_packing(gn_batch* b, int warp_max_vertices);
+gn_status gn_batch_packing(const gn_batch* b, int* warp_max_vertices, int* warp_instances);
+
+/* Autotuner: times the batch kernel for max_iters iterations (twice each) at every CTA size
+ * {256, 512, 1024} crossed with every packing threshold {0, 64, 128, 256, 512} that moves a
+ * different set of instances into warp mode, and keeps the fastest pair; *threads_out receives
+ * the CTA size (may be NULL), gn_batch_packing the threshold. */
 gn_status gn_batch_tune(gn_batch* b, const gn_params* p, int max_iters, int* threads_out);
 
 /* gn_extract_is for every instance of the last run: mask uint8[vtx_off[count]], counts int32[count],

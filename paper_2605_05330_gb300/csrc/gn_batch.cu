@@ -5,6 +5,11 @@
 // longest-processing-time first), keeps the whole instance in shared memory and iterates it to
 // its own stop test (per-instance convergence: a finished instance frees its CTA for the next
 // one), then writes its state and summary.  No grid-wide synchronisation exists.
+// Packing: instances up to a size threshold form a second queue, run a warp per instance (a
+// CTA's warps take them one by one, each in its own slice of the CTA's shared memory, with warp
+// synchronisation only) once the CTA queue is empty.  A warp sums a row with the same lanes and
+// in the same order as a CTA, so both modes give the same iterates bit for bit.  The CTA size
+// and the threshold are the autotuner's choices (gn_batch_tune).
 //
 // Two instance kinds:
 //   GN_INSTANCE_CSR         a general graph given as CSR (local ids); G lanes per row
@@ -66,6 +71,8 @@ struct BatchParams {
   int nmax;                 // largest instance (the state arrays of the shared-memory layout)
   int ncsr;                 // largest CSR instance (its neighbour sums and row offsets)
   int idcap;                // local ids held in shared memory up to this many entries
+  int nbig;                 // order[0, nbig): CTA per instance; order[nbig, count): warp per instance
+  int wbytes;               // shared memory of one warp in warp mode (multiple of 16)
 };
 
 static constexpr int kBatchMaxThreads = 1024;
@@ -104,6 +111,166 @@ __device__ __forceinline__ dev::f2 block_sum_pair(dev::f2 v, float* shh, float* 
   return t;
 }
 
+// Bytes of shared memory an instance needs in warp mode: six state arrays (y_hi, y_lo, x, v_hi,
+// v_lo, neighbour sums) and, for a CSR instance, its row offsets and 16-bit local ids; for an
+// assignment instance its row and column sums as float pairs.
+__host__ __device__ __forceinline__ int warp_bytes(int n, int nnz, int kind) {
+  const int base = 4 * 6 * n;
+  if (kind == GN_INSTANCE_ASSIGNMENT) {
+    const int kk = (int)lrint(sqrt((double)n));
+    return base + 16 * kk;
+  }
+  return base + 4 * (n + 1) + ((2 * nnz + 15) & ~15);
+}
+
+// Warp mode: each warp takes instances from the second queue and runs each to its stop test with
+// warp synchronisation only.  The per-row arithmetic is the CTA mode's: G lanes per CSR row with
+// the same lane split and shuffle order, lane-sequential row and column sums for an assignment
+// instance, the same update and the same stop decision (max and count reductions, exact).
+__device__ void run_warp_instances(const BatchParams& P, unsigned char* smem) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wsm = smem + (size_t)warp * (size_t)P.wbytes;
+  const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
+  for (;;) {
+    unsigned q = 0;
+    if (lane == 0) q = atomicAdd(P.queue + 1, 1u);
+    q = __shfl_sync(0xffffffffu, q, 0);
+    if (q >= (unsigned)(P.count - P.nbig)) return;
+    const int inst = P.order[P.nbig + q];
+    const int64_t v0 = P.vtx_off[inst];
+    const int n = (int)(P.vtx_off[inst + 1] - v0);
+    const int kind = P.kind[inst];
+    const int64_t e0 = P.ent_off[inst];
+    const int nnz = (int)(P.ent_off[inst + 1] - e0);
+    const int32_t* rp_g = P.row_ptr + v0 + inst;
+    const int32_t* ci_g = P.col_idx + e0;
+    const int kk = kind == GN_INSTANCE_ASSIGNMENT ? (int)lrintf(sqrtf((float)n)) : 0;
+    const int G = P.group[inst];
+    float* s_yh = reinterpret_cast<float*>(wsm);
+    float* s_yl = s_yh + n;
+    float* s_x = s_yl + n;
+    float* s_vh = s_x + n;
+    float* s_vl = s_vh + n;
+    float* s_sum = s_vl + n;
+    int* s_rp = reinterpret_cast<int*>(s_sum + n);        // CSR
+    float* s_rs = s_sum + n;                              // assignment: rh, rl, ch, cl (kk each)
+    uint16_t* s_id = reinterpret_cast<uint16_t*>(s_rp + n + 1);
+    for (int i = lane; i < n; i += 32) {
+      const float xi = P.x[v0 + i];
+      const dev::f2 vv = {P.v[v0 + i], P.vlo[v0 + i]};
+      const dev::f2 yy = dev::mul_f2(vv, dev::f2{xi, 0.0f});
+      s_x[i] = xi;
+      s_vh[i] = vv.hi;
+      s_vl[i] = vv.lo;
+      s_yh[i] = yy.hi;
+      s_yl[i] = yy.lo;
+    }
+    if (kind == GN_INSTANCE_CSR) {
+      for (int i = lane; i <= n; i += 32) s_rp[i] = rp_g[i];
+      for (int e = lane; e < nnz; e += 32) s_id[e] = (uint16_t)ci_g[e];
+    }
+    __syncwarp();
+    unsigned long long hits = 0;
+    int k = 0, stop = 0;
+    float last_r = 0.0f;
+    unsigned last_n = 0;
+    dev::f2 last_obj = {0.0f, 0.0f};
+    float last_l1 = 0.0f, last_en = 0.0f;
+    for (; k < P.k_end; ++k) {
+      const float2 gg = P.gtab[k < P.gtab_len ? k : P.gtab_len - 1];
+      const dev::f2 gam = {gg.x, gg.y};
+      if (kind == GN_INSTANCE_CSR) {
+        const int grp = lane / G, gl = lane & (G - 1), ngrp = 32 / G;
+        for (int base = 0; base < n; base += ngrp) {
+          const int r = base + grp;
+          float acc = 0.0f;
+          if (r < n) {
+            const int a = s_rp[r], c = s_rp[r + 1];
+            for (int e = a + gl; e < c; e += G) acc += s_yh[s_id[e]];
+          }
+          for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (r < n && gl == 0) s_sum[r] = acc;
+        }
+      } else {
+        for (int t = lane; t < 2 * kk; t += 32) {
+          const bool row = t < kk;
+          const int q2 = row ? t : t - kk;
+          dev::f2 a = {0.0f, 0.0f};
+          for (int j = 0; j < kk; ++j) {
+            const float yv = row ? s_yh[q2 * kk + j] : s_yh[j * kk + q2];
+            const dev::f2 s = dev::two_sum(a.hi, yv);
+            a = dev::fast_two_sum(s.hi, dev::fadd(s.lo, a.lo));
+          }
+          s_rs[(row ? 0 : 2 * kk) + q2] = a.hi;
+          s_rs[(row ? kk : 3 * kk) + q2] = a.lo;
+        }
+      }
+      __syncwarp();
+      const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
+      CheckAcc acc;
+      for (int i = lane; i < n; i += 32) {
+        Own o = {s_yh[i], s_yl[i], s_x[i]};
+        float sn;
+        if (kind == GN_INSTANCE_CSR) {
+          sn = s_sum[i];
+        } else {
+          const int r = i / kk, c = i - r * kk;
+          const float yv = o.pub;
+          dev::f2 a = dev::two_sum(s_rs[r], -yv);
+          a.lo = dev::fadd(a.lo, s_rs[kk + r]);
+          dev::f2 b = dev::two_sum(s_rs[2 * kk + c], -yv);
+          b.lo = dev::fadd(b.lo, s_rs[3 * kk + c]);
+          const dev::f2 t = dev::two_sum(a.hi, b.hi);
+          sn = dev::fadd(t.hi, dev::fadd(t.lo, dev::fadd(a.lo, b.lo)));
+        }
+        update_one(o, dev::f2{s_vh[i], s_vl[i]}, sn, gam, check, check ? P.w[v0 + i] : 0.0f, th_lo, th_hi, hits,
+                   acc);
+        s_yh[i] = o.pub;
+        s_yl[i] = o.aux;
+        s_x[i] = o.xs;
+      }
+      __syncwarp();
+      if (check) {
+        const float r = dev::warp_max(acc.rmax);
+        const unsigned nb = dev::warp_sum_u(acc.nonbin);
+        const dev::f2 ob = dev::warp_sum_f2(acc.obj);
+        const dev::f2 dg = dev::two_sum(gg.x, -P.thr_hi);
+        const bool bin_ok = nb == 0u && dev::fadd(dg.hi, dev::fadd(dg.lo, dev::fsub(gg.y, P.thr_lo))) > 0.0f;
+        const bool res_ok = P.res_test && r <= P.tol_f;
+        last_r = r;
+        last_n = nb;
+        last_obj = ob;
+        last_l1 = acc.l1;
+        last_en = acc.en;
+        if (bin_ok || res_ok) {
+          stop = 1;
+          ++k;
+          break;
+        }
+      }
+    }
+    for (int i = lane; i < n; i += 32) P.x[v0 + i] = own_x(Own{s_yh[i], s_yl[i], s_x[i]}, s_vh[i]);
+    const dev::f2 l1s = dev::warp_sum_f2(last_l1);
+    const dev::f2 ens = dev::warp_sum_f2(last_en);
+    const unsigned long long h = dev::warp_sum_ull(hits);
+    if (lane == 0) {
+      BatchInfoDev bi;
+      bi.iters = k;
+      bi.converged = stop;
+      bi.binary = last_n == 0u;
+      bi.nonbin = last_n;
+      bi.hits = h;
+      bi.resid_inf = last_r;
+      bi.pad = 0.0f;
+      bi.objective = (double)last_obj.hi + (double)last_obj.lo;
+      bi.resid_l1 = (double)l1s.hi + (double)l1s.lo;
+      bi.energy = (double)ens.hi + (double)ens.lo;
+      P.info[inst] = bi;
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_inst;
@@ -133,12 +300,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
   for (;;) {
     if (tid == 0) {
       const unsigned q = atomicAdd(P.queue, 1u);
-      s_inst = q < (unsigned)P.count ? P.order[q] : -1;
+      s_inst = q < (unsigned)P.nbig ? P.order[q] : -1;
     }
     __syncthreads();
     const int inst = s_inst;
     __syncthreads();
-    if (inst < 0) return;
+    if (inst < 0) break;
     const int64_t v0 = P.vtx_off[inst];
     const int n = (int)(P.vtx_off[inst + 1] - v0);
     const int kind = P.kind[inst];
@@ -280,6 +447,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
     }
     __syncthreads();
   }
+  // warp mode for the small instances
+  if (P.nbig < P.count) run_warp_instances(P, smem);
 }
 
 // ---- validation and preparation kernels (thread per global vertex)
@@ -505,6 +674,11 @@ struct gn_batch {
   int ctas = 0;
   int idcap = 0;
   size_t smem = 0;
+  int wmax = 0;                         // instances up to this many vertices run a warp each (0: none)
+  int wbytes = 0;                       // shared memory of one warp in warp mode
+  int nbig = 0;                         // instances in CTA mode (the rest: warp mode)
+  std::vector<double> h_work;           // per instance: work estimate, size, entries, kind
+  std::vector<int> h_n, h_e, h_kind;
   // captured run
   cudaGraphExec_t graph = nullptr;
   struct Key {
@@ -519,6 +693,25 @@ struct gn_batch {
 };
 
 namespace gn {
+
+// the processing order: CTA-mode instances by decreasing work, then the warp-mode ones (at most
+// wmax vertices and fitting one warp's share of shared memory) by decreasing work
+static gn_status batch_order(gn_batch* b) {
+  std::vector<int32_t> big, small;
+  for (int i = 0; i < b->count; ++i) {
+    const bool w = b->wmax > 0 && b->h_n[i] <= b->wmax && warp_bytes(b->h_n[i], b->h_e[i], b->h_kind[i]) <= b->wbytes;
+    (w ? small : big).push_back(i);
+  }
+  auto by_work = [&](int a, int c) { return b->h_work[a] > b->h_work[c]; };
+  std::stable_sort(big.begin(), big.end(), by_work);
+  std::stable_sort(small.begin(), small.end(), by_work);
+  b->nbig = (int)big.size();
+  big.insert(big.end(), small.begin(), small.end());
+  if (b->count > 0)
+    GN_CUDA(cudaMemcpyAsync(b->d_order, big.data(), sizeof(int32_t) * b->count, cudaMemcpyHostToDevice, b->stream));
+  GN_CUDA(cudaStreamSynchronize(b->stream));
+  return GN_OK;
+}
 
 static size_t batch_smem(int nmax, int ncsr, int idcap) {
   return sizeof(float) * (5 * (size_t)nmax + 4 * 128 + (size_t)ncsr) + sizeof(int) * ((size_t)ncsr + 4) +
@@ -547,7 +740,8 @@ static gn_status batch_config(gn_batch* b, int threads) {
   b->idcap = idcap;
   b->smem = smem;
   b->ctas = std::min<int64_t>((int64_t)per_sm * b->num_sms, std::max(1, b->count));
-  return GN_OK;
+  b->wbytes = (int)((smem / (size_t)(threads / 32)) & ~(size_t)15);
+  return batch_order(b);
 }
 
 }  // namespace gn
@@ -628,9 +822,14 @@ extern "C" gn_status gn_batch_create(gn_batch** out, int32_t count, const int64_
   b->ntot = vo[count];
   b->etot = eo[count];
   b->h_vtx_off = vo;
-  std::vector<int32_t> order(count);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+  b->h_work = work;
+  b->h_n.resize(count);
+  b->h_e.resize(count);
+  b->h_kind.assign(kd.begin(), kd.begin() + count);
+  for (int i = 0; i < count; ++i) {
+    b->h_n[i] = (int)(vo[i + 1] - vo[i]);
+    b->h_e[i] = (int)(eo[i + 1] - eo[i]);
+  }
 
   const size_t nv = (size_t)std::max<int64_t>(b->ntot, 1);
   GN_CUDA(cudaMalloc(&b->d_vtx_off, sizeof(int64_t) * (count + 1)));
@@ -660,7 +859,6 @@ extern "C" gn_status gn_batch_create(gn_batch** out, int32_t count, const int64_
   GN_CUDA(cudaMemcpyAsync(b->d_vtx_off, vo.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, b->stream));
   GN_CUDA(cudaMemcpyAsync(b->d_ent_off, eo.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, b->stream));
   GN_CUDA(cudaMemcpyAsync(b->d_kind, kd.data(), sizeof(int32_t) * std::max(count, 1), cudaMemcpyHostToDevice, b->stream));
-  GN_CUDA(cudaMemcpyAsync(b->d_order, order.data(), sizeof(int32_t) * std::max(count, 1), cudaMemcpyHostToDevice, b->stream));
   GN_CUDA(cudaMemcpyAsync(b->d_group, grp.data(), sizeof(int32_t) * std::max(count, 1), cudaMemcpyHostToDevice, b->stream));
   if (b->ntot > 0) {
     if (!w) return fail(GN_ERR_ARG, "gn_batch_create: w is NULL");
@@ -706,12 +904,30 @@ extern "C" gn_status gn_batch_set_threads(gn_batch* b, int threads) {
   return batch_config(b, threads);
 }
 
+extern "C" gn_status gn_batch_set_packing(gn_batch* b, int warp_max_vertices) {
+  using namespace gn;
+  if (!b || warp_max_vertices < 0) return fail(GN_ERR_ARG, "gn_batch_set_packing: bad argument");
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->wmax = warp_max_vertices;
+  return batch_order(b);
+}
+
+extern "C" gn_status gn_batch_packing(const gn_batch* b, int* warp_max_vertices, int* warp_instances) {
+  if (!b) return gn::fail(GN_ERR_ARG, "gn_batch_packing: NULL handle");
+  if (warp_max_vertices) *warp_max_vertices = b->wmax;
+  if (warp_instances) *warp_instances = b->count - b->nbig;
+  return GN_OK;
+}
+
 namespace gn {
 
 // the run sequence on the handle's stream (captured into a graph by gn_batch_run)
 static gn_status batch_enqueue(gn_batch* b, const float* x0_dev, int max_iters, double tol, const gn_params& p) {
   const int glen = (p.gamma_mode == GN_GAMMA_FIXED || p.ramp_iters <= 1) ? 1 : std::max(1, std::min(max_iters, p.ramp_iters));
-  GN_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned), b->stream));
+  GN_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(unsigned) * 2, b->stream));  // CTA and warp queues
   GN_CUDA(cudaMemsetAsync(b->d_flags, 0, sizeof(int) * 4, b->stream));
   k_batch_gamma<<<(glen + 255) / 256, 256, 0, b->stream>>>(glen, p.gamma_mode, p.gamma0, p.gamma1, p.ramp_iters,
                                                           b->d_gtab);
@@ -753,6 +969,8 @@ static gn_status batch_enqueue(gn_batch* b, const float* x0_dev, int max_iters, 
   P.nmax = b->nmax;
   P.ncsr = b->ncsr;
   P.idcap = b->idcap;
+  P.nbig = b->nbig;
+  P.wbytes = b->wbytes;
   k_gn_batch<<<b->ctas, b->threads, b->smem, b->stream>>>(P);
   GN_LAUNCHED();
   GN_CUDA(cudaMemcpyAsync(b->h_info, b->d_info, sizeof(BatchInfoDev) * b->count, cudaMemcpyDeviceToHost, b->stream));
@@ -861,23 +1079,35 @@ extern "C" float gn_batch_last_ms(gn_batch* b) {
 extern "C" gn_status gn_batch_tune(gn_batch* b, const gn_params* p, int max_iters, int* threads_out) {
   using namespace gn;
   if (!b || max_iters < 1) return fail(GN_ERR_ARG, "gn_batch_tune: bad argument");
-  const int cand[] = {256, 512, 1024};
+  // the schedule: CTA size x the size threshold of warp mode (0: every instance a CTA); a
+  // threshold that moves no further instance into warp mode than a smaller one is skipped
+  const int cand_t[] = {256, 512, 1024};
+  const int cand_w[] = {0, 64, 128, 256, 512};
   float best = 1e30f;
-  int best_t = b->threads;
-  for (int t : cand) {
-    gn_status st = gn_batch_set_threads(b, t);
-    if (st != GN_OK) continue;
-    float acc = 0.0f;
-    for (int rep = 0; rep < 2; ++rep) {
-      st = gn_batch_run(b, nullptr, max_iters, -1.0, p, nullptr, nullptr);
-      if (st < 0) return st;
-      if (rep) acc += gn_batch_last_ms(b);
-    }
-    if (acc < best) {
-      best = acc;
-      best_t = t;
+  int best_t = b->threads, best_w = b->wmax;
+  for (int t : cand_t) {
+    int last_small = -1;
+    for (int wm : cand_w) {
+      b->wmax = wm;
+      gn_status st = gn_batch_set_threads(b, t);
+      if (st != GN_OK) break;
+      const int nsmall = b->count - b->nbig;
+      if (nsmall == last_small) continue;
+      last_small = nsmall;
+      float acc = 0.0f;
+      for (int rep = 0; rep < 2; ++rep) {
+        st = gn_batch_run(b, nullptr, max_iters, -1.0, p, nullptr, nullptr);
+        if (st < 0) return st;
+        if (rep) acc += gn_batch_last_ms(b);
+      }
+      if (acc < best) {
+        best = acc;
+        best_t = t;
+        best_w = wm;
+      }
     }
   }
+  b->wmax = best_w;
   gn_status st = gn_batch_set_threads(b, best_t);
   if (st != GN_OK) return st;
   if (threads_out) *threads_out = best_t;

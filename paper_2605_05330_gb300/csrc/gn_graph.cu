@@ -298,6 +298,51 @@ extern "C" gn_status gn_set_io(gn_graph* g, int mem) {
 
 void gn_free_record(gn_graph* g);  // gn_adjoint.cu
 
+namespace gn {
+// finite and positive, nothing else: the flag only
+__global__ void k_check_weights(int n, const float* __restrict__ w, int* flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (!(w[i] > 0.0f) || !isfinite(w[i]))) atomicOr(flags, DEV_BAD_WEIGHT);
+}
+}  // namespace gn
+
+extern "C" gn_status gn_set_weights(gn_graph* g, const float* w) {
+  using namespace gn;
+  if (!g || (g->n > 0 && !w)) return fail(GN_ERR_ARG, "gn_set_weights: bad argument");
+  const int n = g->n;
+  if (n == 0) return GN_OK;
+  GN_CUDA(cudaSetDevice(g->device));
+  const float* w_dev = nullptr;  // caller order
+  gn_status st = upload_or_alias(g, w, sizeof(float) * n, (const void**)&w_dev);
+  if (st != GN_OK) return st;
+  // validate first, so that a rejected vector leaves the handle's weights as they were
+  GN_CUDA(cudaMemsetAsync(g->d_flags, 0, sizeof(int) * 8, g->stream));
+  k_check_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, w_dev, g->d_flags);
+  GN_LAUNCHED();
+  GN_CUDA(cudaMemcpyAsync(g->h_flags, g->d_flags, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->h_flags[0] & DEV_BAD_WEIGHT) return fail(GN_ERR_WEIGHT, "gn_set_weights: weight <= 0 or not finite");
+  if (g->d_perm) {
+    k_permute_w<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_perm, w_dev, g->d_w);
+    GN_LAUNCHED();
+  } else {
+    GN_CUDA(cudaMemcpyAsync(g->d_w, w_dev, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
+  }
+  k_weights<<<grid_for(n, 256), 256, 0, g->stream>>>(n, g->d_w, g->d_v, g->d_vlo, g->d_flags);
+  GN_LAUNCHED();
+  GN_CUDA(cudaGetLastError());
+  // what depended on the old weights: the recorded forward, a state to resume from, and the
+  // one-instance batch of the CTA kernel (built again on its next use)
+  gn_free_record(g);
+  if (g->cta) {
+    gn_batch_destroy(g->cta);
+    g->cta = nullptr;
+  }
+  g->has_state = false;
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  return GN_OK;
+}
+
 extern "C" void gn_destroy(gn_graph* g) {
   if (!g) return;
   int cur = 0;

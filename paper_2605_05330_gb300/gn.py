@@ -94,6 +94,8 @@ def lib():
         L.gn_destroy.restype = None
         L.gn_set_io.argtypes = [P, ctypes.c_int]
         L.gn_set_io.restype = ctypes.c_int
+        L.gn_set_weights.argtypes = [P, P]
+        L.gn_set_weights.restype = ctypes.c_int
         L.gn_num_vertices.argtypes = [P]
         L.gn_num_vertices.restype = ctypes.c_int32
         L.gn_num_entries.argtypes = [P]
@@ -203,6 +205,12 @@ class Graph:
         _check(lib().gn_set_io(self._h, DEVICE if device else HOST))
         self.device_io = device
 
+    def set_weights(self, w):
+        """New vertex weights on the same graph (gn_set_weights)."""
+        if not self.device_io:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(lib().gn_set_weights(self._h, _ptr(w)))
+
     def _alloc(self, dtype, n):
         if self.device_io:
             import torch
@@ -288,6 +296,10 @@ def _batch_lib():
         L.gn_batch_tune.restype = ctypes.c_int
         L.gn_batch_extract.argtypes = [P, P, P, P, P]
         L.gn_batch_extract.restype = ctypes.c_int
+        L.gn_batch_set_packing.argtypes = [P, ctypes.c_int]
+        L.gn_batch_set_packing.restype = ctypes.c_int
+        L.gn_batch_packing.argtypes = [P, P, P]
+        L.gn_batch_packing.restype = ctypes.c_int
         L._batch_ready = True
     return L
 
@@ -385,6 +397,17 @@ class Batch:
     def set_threads(self, t):
         _check(_batch_lib().gn_batch_set_threads(self._h, int(t)))
 
+    def set_packing(self, warp_max_vertices):
+        """Instances of at most this many vertices run a warp each (gn_batch_set_packing)."""
+        _check(_batch_lib().gn_batch_set_packing(self._h, int(warp_max_vertices)))
+
+    def packing(self):
+        """(threshold, number of instances in warp mode) (gn_batch_packing)."""
+        a, c = ctypes.c_int(0), ctypes.c_int(0)
+        _check(_batch_lib().gn_batch_packing(self._h, ctypes.cast(ctypes.pointer(a), P),
+                                             ctypes.cast(ctypes.pointer(c), P)))
+        return a.value, c.value
+
     def tune(self, params: Params | None = None, max_iters=200):
         p = params if params is not None else default_params()
         t = ctypes.c_int(0)
@@ -448,14 +471,18 @@ def _grad_function():
         backward is the library's adjoint (gn_backward) with sqrt(T) checkpointing."""
 
         @staticmethod
-        def forward(ctx, row_ptr, col_idx, w, x0, iters, params, start_iter):
+        def forward(ctx, row_ptr, col_idx, w, x0, iters, params, start_iter, graph):
             p = params if params is not None else default_params()
             p = default_params(**{f: getattr(p, f) for f, _ in Params._fields_})
             p.record = 1
-            g = Graph(row_ptr, col_idx, w.detach())
+            if graph is None:
+                g, own = Graph(row_ptr, col_idx, w.detach()), True
+            else:
+                g, own = graph, False
+                g.set_weights(w.detach().contiguous())
             x, info = g.run(x0=x0.detach().contiguous(), max_iters=start_iter + iters, tol=-1.0, params=p,
                             start_iter=start_iter)
-            ctx.graph = g
+            ctx.graph, ctx.own = g, own
             ctx.info = info
             return x
 
@@ -463,9 +490,10 @@ def _grad_function():
         def backward(ctx, gx):
             g = ctx.graph
             dw, dx0 = g.backward(gx.contiguous().to(torch.float32))
-            g.close()
+            if ctx.own:
+                g.close()
             ctx.graph = None
-            return None, None, dw, dx0, None, None, None
+            return None, None, dw, dx0, None, None, None, None
 
     return UnrolledGN
 
@@ -473,9 +501,14 @@ def _grad_function():
 _unrolled = None
 
 
-def unrolled_gn(row_ptr, col_idx, w, x0, iters, params: Params | None = None, start_iter=0):
-    """Differentiable GN on CUDA tensors: returns x_T (float32[n]); gradients flow to w and x0."""
+def unrolled_gn(row_ptr, col_idx, w, x0, iters, params: Params | None = None, start_iter=0, graph=None):
+    """Differentiable GN on CUDA tensors: returns x_T (float32[n]); gradients flow to w and x0.
+
+    graph: an existing device-I/O Graph of the same CSR to run on (its weights are replaced by w
+    with gn_set_weights, so the CSR is neither validated nor laid out again); it holds the
+    recorded run until backward, so one graph serves one forward/backward pair at a time.
+    Without it each forward builds and frees a handle of its own."""
     global _unrolled
     if _unrolled is None:
         _unrolled = _grad_function()
-    return _unrolled.apply(row_ptr, col_idx, w, x0, int(iters), params, int(start_iter))
+    return _unrolled.apply(row_ptr, col_idx, w, x0, int(iters), params, int(start_iter), graph)

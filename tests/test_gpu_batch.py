@@ -131,6 +131,33 @@ def test_batch_graph_replay_tune_and_device_io(gn):
     assert [d["iters"] for d in i1] == [d["iters"] for d in i4]
 
 
+@pytest.mark.parametrize("threads", [256, 512])
+def test_warp_packing_is_bit_identical(gn, threads):
+    """Instance packing: the small instances run a warp each, several per CTA, after the CTA
+    queue; both kinds give the iterates and stop of CTA mode bit for bit, for fixed steps and for
+    the run to a binary state."""
+    specs = [s for s in small_specs(count=48, seed=783)]
+    items = batch_items(specs)
+    b = gn.Batch(items)
+    b.set_threads(threads)
+    run_kw, pk = fixed_steps(20)
+    ref = [b.run(params=gn.default_params(**pk), **run_kw), b.run(max_iters=2000, tol=1e-7)]
+    thr = 128 if threads == 512 else 256
+    b.set_packing(thr)
+    wm, moved = b.packing()
+    assert wm == thr and moved > 0
+    # both kinds have instances this small (whether each fits a warp's share is the library's call)
+    small = {isinstance(s, tuple) for s in specs if (s[1] * s[1] if isinstance(s, tuple) else s.n) <= thr}
+    assert small == {True, False}
+    got = [b.run(params=gn.default_params(**pk), **run_kw), b.run(max_iters=2000, tol=1e-7)]
+    for (xa, ia), (xb, ib) in zip(ref, got):
+        np.testing.assert_array_equal(xa, xb)
+        assert [d["iters"] for d in ia] == [d["iters"] for d in ib]
+        assert [d["safe_div_hits"] for d in ia] == [d["safe_div_hits"] for d in ib]
+    st, mask, counts, weights, statuses = b.extract()
+    assert st in ("OK", "WARN_NOT_MAXIMAL")
+
+
 def test_batch_validation(gn):
     good = inputs.er_graph(50, 4, 782)
     bad = inputs.GraphInstance("asym", np.array([0, 1, 1], np.int32), np.array([1], np.int32),

@@ -1,12 +1,19 @@
 """Differentiable GN: the library's adjoint (gn_backward, sqrt(T) checkpointing) against the FP64
 autograd reference of the unrolled x-space iteration (itself pinned to central finite
-differences), on a 200-vertex BFS ball of the ER n=50,000 degree-12 graph and at full size.
+differences), on 200- and 2000-vertex BFS balls of the ER n=50,000 degree-12 graph and at full
+size.
 
 Tolerance: the adjoint runs in FP32 (log-space adjoint, float-pair states); the bar is a
 relative error of the gradient vector (2-norm) of 1e-3 and entrywise 1e-3 of the largest
-entry, plus an absolute floor of 1e-6 for the FP32 rounding of terms that cancel exactly
-(once the pursuit has binarised the state the true gradient is ~1e-24 and that floor is all
-that is left to compare).
+entry, plus an absolute floor of 1e-6 for the FP32 rounding of terms that cancel exactly.
+Every case checks that its reference gradients stand far above that floor (once the pursuit
+has binarised the state the true gradient is ~1e-24, so such runs would compare the floor
+only).
+
+Also: the autograd function on a handle the caller keeps (gn_set_weights replaces the weights,
+no second layout build) equals the one that builds its own handle, bit for bit, over several
+forward/backward pairs with different weights; gn_set_weights itself equals a fresh handle and
+rejects bad weights without touching the old ones.
 """
 import numpy as np
 import pytest
@@ -46,15 +53,23 @@ def _reference(inst, x0, g, T, mode=0, gamma1=1.5):
                                grad.gammas(T, mode=mode, gamma1=gamma1))
 
 
-@pytest.mark.parametrize("T,mode,gamma1", [(20, 0, 1.5), (50, 0, 1.5), (200, 0, 1.5), (200, 1, 0.9)])
-def test_gradient_on_bfs_ball(env, T, mode, gamma1):
+# (ball size, T, gamma mode, gamma1): the 200-vertex ball is nearly binary by T = 50 (its
+# gradients fall to 1e-6), so longer runs use a 2000-vertex ball, where at T = 200 about 3%
+# (pursuit) and 11% (fixed gamma = 0.7) of the vertices are still fractional and both
+# gradients are of order 1
+@pytest.mark.parametrize("size,T,mode,gamma1", [(200, 20, 0, 1.5), (2000, 50, 0, 1.5), (2000, 200, 0, 1.5),
+                                                (2000, 200, 1, 0.7)])
+def test_gradient_on_bfs_ball(env, size, T, mode, gamma1):
     torch, gn = env
     big, gvec = inputs.workload_diff()
-    inst = inputs.bfs_ball(big, 0, 200)
+    inst = inputs.bfs_ball(big, 0, size)
     deg = np.diff(inst.row_ptr)
     x0 = (1.0 / (deg + 1.0)).astype(np.float32)
     g = gvec[inst.meta["verts"]]
     L, dw_ref, dx0_ref, xT_ref = _reference(inst, x0, g, T, mode, gamma1)
+    # the comparison is informative: the floor's share of the 2-norm bound is at most 2%
+    floor = 1e-6 * np.sqrt(inst.n)
+    assert np.linalg.norm(dw_ref) > 50 * floor and np.linalg.norm(dx0_ref) > 50 * floor
     G = gn.Graph(inst.row_ptr, inst.col_idx, inst.w)
     x, info = G.run(x0=x0, max_iters=T, tol=-1.0,
                     params=gn.default_params(record=1, gamma_mode=mode, gamma1=gamma1))
@@ -93,3 +108,50 @@ def test_backward_without_record_is_an_error(env):
     with pytest.raises(gn.GNError) as e:
         G.backward(np.ones(inst.n, np.float32))
     assert e.value.status == "ERR_NO_RECORD"
+
+
+def test_autograd_on_a_kept_handle_and_set_weights(env):
+    torch, gn = env
+    inst, gvec = inputs.workload_diff()
+    dev = torch.device("cuda")
+    rp = torch.from_numpy(inst.row_ptr).to(dev)
+    ci = torch.from_numpy(inst.col_idx).to(dev)
+    deg = np.diff(inst.row_ptr)
+    x0 = torch.from_numpy((1.0 / (deg + 1.0)).astype(np.float32)).to(dev)
+    gd = torch.from_numpy(gvec).to(dev)
+    kept = gn.Graph(rp, ci, torch.from_numpy(inst.w).to(dev))
+    rng = np.random.default_rng(17)
+    for rep in range(3):
+        w_np = (inst.w * rng.uniform(0.5, 2.0, inst.n)).astype(np.float32)
+        outs = []
+        for graph in (None, kept):
+            w = torch.from_numpy(w_np).to(dev).requires_grad_(True)
+            x = x0.clone().requires_grad_(True)
+            xT = gn.unrolled_gn(rp, ci, w, x, 50, graph=graph)
+            torch.dot(gd, xT).backward()
+            outs.append((xT.detach().cpu().numpy(), w.grad.cpu().numpy(), x.grad.cpu().numpy()))
+        for a, b in zip(*outs):
+            np.testing.assert_array_equal(a, b)
+    # gn_set_weights: a run equals a fresh handle's; bad weights are refused and change nothing
+    w_np = (inst.w * rng.uniform(0.5, 2.0, inst.n)).astype(np.float32)
+    kept.set_weights(torch.from_numpy(w_np).to(dev))
+    xa, ia = kept.run()
+    fresh = gn.Graph(rp, ci, torch.from_numpy(w_np).to(dev))
+    xb, ib = fresh.run()
+    np.testing.assert_array_equal(xa.cpu().numpy(), xb.cpu().numpy())
+    assert ia["iters"] == ib["iters"]
+    bad = torch.from_numpy(w_np).to(dev)
+    bad[7] = float("nan")
+    with pytest.raises(gn.GNError) as e:
+        kept.set_weights(bad)
+    assert e.value.status == "ERR_WEIGHT"
+    xc, ic = kept.run()
+    np.testing.assert_array_equal(xa.cpu().numpy(), xc.cpu().numpy())
+    # a recorded run does not survive new weights
+    kept.run(max_iters=10, tol=-1.0, params=gn.default_params(record=1))
+    kept.set_weights(torch.from_numpy(w_np).to(dev))
+    with pytest.raises(gn.GNError) as e:
+        kept.backward(torch.ones(inst.n, device=dev))
+    assert e.value.status == "ERR_NO_RECORD"
+    kept.close()
+    fresh.close()
