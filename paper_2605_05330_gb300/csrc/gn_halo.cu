@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   // iteration k - 1 (after a check); the first iteration waits for the prologue's pushes
   bool synced = false;
   bool fail = false;
+  int next_chk = (P.k_start / P.check_every + 1) * P.check_every;  // a check follows step next_chk - 1
 
   for (; stop != 2 && k < P.k_end; ++k) {
     const int r = k - P.k_start;
@@ -313,7 +314,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     }
 
     // 4. update and stop-test partials
-    const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
+    const bool due = k + 1 == next_chk;
+    const bool check = due || (k + 1 == P.k_end);
+    if (due) next_chk += P.check_every;
     CheckAcc acc;
     if (REG) {
       // A warp with a second row somewhere computes both rows' arithmetic first (no branch

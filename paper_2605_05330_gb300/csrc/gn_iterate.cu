@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   int nchk = 0;  // checks so far (selects the check word)
   int k = P.k_start;
   const int grp = tid / G, gl = tid & (G - 1), ngrp = blockDim.x / G;
+  int next_chk = (P.k_start / P.check_every + 1) * P.check_every;  // a check follows step next_chk - 1
 
   for (; k < P.k_end; ++k) {
     const dev::f2 gam = {T.gh, T.gl};
@@ -126,7 +127,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
     __syncthreads();
 
     // ---- update, stop-test partials, barrier, stop decision
-    const bool check = ((k + 1) % P.check_every == 0) || (k + 1 == P.k_end);
+    const bool due = k + 1 == next_chk;
+    const bool check = due || (k + 1 == P.k_end);
+    if (due) next_chk += P.check_every;
     CheckAcc acc;
     update_rows(S, nr, rb, P.w, yout, gam, check, th_lo, th_hi, hits, acc);
     gamma_store(gnext, T);  // visible to every thread after the barrier's __syncthreads
