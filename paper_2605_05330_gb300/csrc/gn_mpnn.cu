@@ -200,6 +200,98 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense_fwd(int n, const float*
 template <int DIN>
 constexpr size_t dense_fwd_smem() { return sizeof(float) * (size_t)kDenseRows * (2 * DIN + 1); }
 
+// ---- the hidden layers (DIN = kH) on the tensor cores: Z = [H | M] W^T + b as a GEMM with
+// K = 2 kH = 128 and N = kH = 64, mma.sync m16n8k16 with bf16 operands and FP32 accumulation.
+// The weights are bf16 already (exact operands).  Each FP32 activation a is split into
+// a_hi = bf16(a) and a_lo = bf16(a - a_hi), and both halves are multiplied: the operand keeps
+// about 16 bits (|a - a_hi - a_lo| <= 2^-17 |a|), so the layer stays at FP32-grade precision
+// instead of rounding the activations to bf16.  A warp computes 16 rows x 64 outputs (eight n8
+// tiles, 32 accumulators per thread) from fragments loaded straight from global memory (each
+// 16-byte-per-row request fills whole 32-byte sectors); the weights sit in shared memory,
+// rows padded so that a fragment's 32 words fall in 32 banks.
+static constexpr int kTcWarps = 4;                 // warps per CTA, 16 rows each
+static constexpr int kTcRows = 16 * kTcWarps;      // rows per CTA tile
+static constexpr int kTcK = 2 * kH;                // [H | M]
+static constexpr int kTcPad = kTcK + 8;            // bf16 per weight row in shared memory
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);  // .x (low half) = lo_elem
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+// split two FP32 values into their bf16 high parts and the bf16 rounding of the remainders
+__device__ __forceinline__ void split_bf16x2(float2 a, uint32_t& hi, uint32_t& lo) {
+  const float hx = __bfloat162float(__float2bfloat16_rn(a.x));
+  const float hy = __bfloat162float(__float2bfloat16_rn(a.y));
+  hi = pack_bf16x2(hx, hy);
+  lo = pack_bf16x2(a.x - hx, a.y - hy);
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float2 load_pair(const float* __restrict__ X, int row, int col, int n) {
+  return row < n ? *reinterpret_cast<const float2*>(X + (size_t)row * kH + col) : make_float2(0.0f, 0.0f);
+}
+
+__global__ void __launch_bounds__(32 * kTcWarps) k_dense_fwd_tc(int n, const float* __restrict__ H,
+                                                                const float* __restrict__ M,
+                                                                const __nv_bfloat16* __restrict__ Wb,
+                                                                float* __restrict__ Z, float* __restrict__ Hout) {
+  __shared__ __align__(16) __nv_bfloat16 sW[kH][kTcPad];  // W[o][k], k over [Ws | Wn]
+  __shared__ float sb[kH];
+  for (int t = threadIdx.x; t < 2 * kH * kH; t += blockDim.x) {
+    const int m = t / (kH * kH), rem = t % (kH * kH), o = rem / kH, k = rem % kH;
+    sW[o][m * kH + k] = Wb[t];
+  }
+  for (int t = threadIdx.x; t < kH; t += blockDim.x) sb[t] = __bfloat162float(Wb[2 * kH * kH + t]);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int ntiles = (n + kTcRows - 1) / kTcRows;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ra = tile * kTcRows + warp * 16 + g, rb = ra + 8;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      acc[j][0] = acc[j][2] = sb[8 * j + 2 * q];
+      acc[j][1] = acc[j][3] = sb[8 * j + 2 * q + 1];
+    }
+#pragma unroll 2
+    for (int ks = 0; ks < kTcK / 16; ++ks) {
+      const float* __restrict__ X = ks < kH / 16 ? H : M;
+      const int c = (ks & (kH / 16 - 1)) * 16 + 2 * q;
+      uint32_t ahi[4], alo[4];
+      split_bf16x2(load_pair(X, ra, c, n), ahi[0], alo[0]);
+      split_bf16x2(load_pair(X, rb, c, n), ahi[1], alo[1]);
+      split_bf16x2(load_pair(X, ra, c + 8, n), ahi[2], alo[2]);
+      split_bf16x2(load_pair(X, rb, c + 8, n), ahi[3], alo[3]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&sW[8 * j + g][16 * ks + 2 * q]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&sW[8 * j + g][16 * ks + 2 * q + 8]);
+        mma_bf16(acc[j], alo, b0, b1);
+        mma_bf16(acc[j], ahi, b0, b1);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int col = 8 * j + 2 * q;
+      if (ra < n) {
+        if (Z) *reinterpret_cast<float2*>(Z + (size_t)ra * kH + col) = make_float2(acc[j][0], acc[j][1]);
+        *reinterpret_cast<float2*>(Hout + (size_t)ra * kH + col) =
+            make_float2(fmaxf(acc[j][0], 0.0f), fmaxf(acc[j][1], 0.0f));
+      }
+      if (rb < n) {
+        if (Z) *reinterpret_cast<float2*>(Z + (size_t)rb * kH + col) = make_float2(acc[j][2], acc[j][3]);
+        *reinterpret_cast<float2*>(Hout + (size_t)rb * kH + col) =
+            make_float2(fmaxf(acc[j][2], 0.0f), fmaxf(acc[j][3], 0.0f));
+      }
+    }
+  }
+}
+
 // dZ = dHout (.) [Z > 0]; dH = dZ Ws, dM = dZ Wn (per row); kRows rows per CTA
 template <int DIN>
 // (dM may alias dHout: each CTA reads its rows of dHout before the barrier and writes them after)
@@ -546,8 +638,9 @@ static gn_status mpnn_forward_impl(gn_mpnn* m, const gn_graph* g, float* x0_out,
     } else {
       k_aggregate<kH><<<blk((int64_t)n * 32, 256), 256, 0, s>>>(n, g->d_row_ptr, g->d_col_idx, Hin, m->Ms[l]);
       GN_LAUNCHED();
-      k_dense_fwd<kH><<<std::min(tiles, 2 * m->num_sms), kDenseThreads, dense_fwd_smem<kH>(), s>>>(
-          n, Hin, m->Ms[l], Wb, Z, m->Hs[l]);
+      const int tc_tiles = (n + kTcRows - 1) / kTcRows;
+      k_dense_fwd_tc<<<std::min(tc_tiles, 8 * m->num_sms), 32 * kTcWarps, 0, s>>>(n, Hin, m->Ms[l], Wb, Z,
+                                                                                 m->Hs[l]);
       GN_LAUNCHED();
     }
     Hin = m->Hs[l];

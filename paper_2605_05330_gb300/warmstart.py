@@ -118,13 +118,24 @@ class WarmStartNet:
         return out
 
 
-def training_graphs(count: int, seed: int = 9000, n_lo: int = 5000, n_hi: int = 50000, avg_deg: float = 10.0):
+def _one_training_graph(args):
+    i, n, seed, avg_deg = args
+    return inputs.unit_disk_graph(int(n), int(n * avg_deg / 2), seed + 1 + i, name=f"train{i}_udg{n}")
+
+
+def training_graphs(count: int, seed: int = 9000, n_lo: int = 5000, n_hi: int = 50000, avg_deg: float = 10.0,
+                    workers: int = 1):
     """Seeded unit-disk graphs with n uniform in [n_lo, n_hi] and the density of the 1M-edge
-    workload (average degree 10), lognormal weights."""
+    workload (average degree 10), lognormal weights.  workers > 1 draws them in that many
+    processes (started with 'spawn'); the graphs do not depend on it."""
     rng = inputs.rng_for(seed)
     ns = rng.integers(n_lo, n_hi + 1, size=count)
-    return [inputs.unit_disk_graph(int(n), int(n * avg_deg / 2), seed + 1 + i, name=f"train{i}_udg{n}")
-            for i, n in enumerate(ns)]
+    jobs = [(i, int(n), seed, avg_deg) for i, n in enumerate(ns)]
+    if workers <= 1 or count < 2:
+        return [_one_training_graph(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_one_training_graph, jobs, chunksize=max(1, count // (4 * workers)))
 
 
 def device_graph(inst, reorder=gn.REORDER_RCM):
@@ -160,18 +171,22 @@ def run_from(graph, x0, gamma0, ramp, max_iters=2000):
     return info, W
 
 
-SCHEDULES = ((0.9, 300), (0.95, 250), (1.0, 200), (1.0, 150), (1.05, 120), (1.1, 80))
-ALPHAS = (0.25, 0.5)
+SCHEDULES = ((0.9, 1000), (0.9, 600), (0.9, 400), (0.9, 300), (0.95, 250), (1.0, 200), (1.0, 150), (1.05, 120),
+             (1.1, 80), (1.2, 50))
+ALPHAS = (0.25, 0.5, 0.75)
 
 
-def pick_schedule(net: WarmStartNet, graphs, gap_max=1e-3, alphas=ALPHAS, schedules=SCHEDULES):
-    """The (alpha, gamma0, ramp) with the fewest mean iterations-to-binary whose warm-started runs
-    stay within gap_max of the paper-schedule cold start on every validation graph (the graphs
-    the form is evaluated on are never used for the choice).  Returns None if no choice does."""
+def pick_schedule(net: WarmStartNet | None, graphs, gap_max=1e-3, alphas=ALPHAS, schedules=SCHEDULES):
+    """The (alpha, gamma0, ramp) with the fewest mean iterations-to-binary over the validation
+    graphs among the choices whose runs stay within gap_max of the paper-schedule cold start on
+    every one of them (the graphs the form is evaluated on are never used for the choice).
+    net None tunes the cold start the same way (alpha 0: x0 = 1/(deg+1), the schedule only), so
+    that the network's gain is measured against a cold start that had the same chance.  Returns
+    None if no choice qualifies."""
     colds = [run_from(g, None, 0.9, 1000) for g in graphs]
     best = None
-    for a in alphas:
-        x0s = [net.predict(g, a) for g in graphs]
+    for a in (alphas if net is not None else (0.0,)):
+        x0s = [net.predict(g, a) if net is not None else None for g in graphs]
         for g0, T in schedules:
             its, ok = [], True
             for g, x0, (ci, Wc) in zip(graphs, x0s, colds):
@@ -181,3 +196,9 @@ def pick_schedule(net: WarmStartNet, graphs, gap_max=1e-3, alphas=ALPHAS, schedu
             if ok and (best is None or np.mean(its) < best[3]):
                 best = (a, g0, T, float(np.mean(its)))
     return best
+
+
+def validation_graphs(count=4, n=50000, seed=9201):
+    """Unit-disk graphs of the training density, seeded apart from the training and evaluation
+    graphs, for the choice of blend and schedule."""
+    return [device_graph(inputs.unit_disk_graph(n, n * 5, seed + 2 * i)) for i in range(count)]
