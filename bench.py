@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / multi-start / ... forms")
-    ap.add_argument("--warm-train", type=int, default=48,
+    ap.add_argument("--warm-train", type=int, default=480,
                     help="training graphs of the learned warm start (the form's network)")
     ap.add_argument("--only", choices=["udg", "ba"], default=None,
                     help="run one graph of the workload (profiling aid; not a bench line)")
