@@ -170,7 +170,7 @@ __device__ void run_warp_instances(const BatchParams& P, unsigned char* smem) {
       for (int e = lane; e < nnz; e += 32) s_id[e] = (uint16_t)ci_g[e];
     }
     __syncwarp();
-    unsigned long long hits = 0;
+    unsigned hits = 0;
     int k = 0, stop = 0;
     float last_r = 0.0f;
     unsigned last_n = 0;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_gn_batch(const BatchPar
     }
     __syncthreads();
 
-    unsigned long long hits = 0;
+    unsigned hits = 0;
     int k = 0, stop = 0;
     float last_r = 0.0f;
     unsigned last_n = 0;

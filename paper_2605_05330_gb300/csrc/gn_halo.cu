@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
   const unsigned halo_bytes = (unsigned)((H.lx + 3) & ~3) * 4u;
 
-  unsigned long long hits = 0;
+  unsigned hits = 0;
   int parity = 0, slot = 0, stop = 0;
   unsigned nbar = 0;
   int nchk = 0;  // checks so far (grid mode: selects the check word)
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
         s0 = update_core(ro[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
         const RowStep s1 = update_core(ro[1], rv[1], in1 ? S.sum[tid + kThreads] : 0.0f, gam);
         if (check && in1) check_terms(s1, ro[1], rv[1], rw[1], th_lo, th_hi, acc);
-        hits += in1 && !s1.ok ? 1ull : 0ull;
+        hits += in1 && !s1.ok ? 1u : 0u;
         ro[1] = s1.next;
         if (in1) {
           s_all[tid + kThreads] = ro[1].pub;
@@ -338,14 +338,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
         s0 = update_core(ro[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
       }
       if (check && in0) check_terms(s0, ro[0], rv[0], rw[0], th_lo, th_hi, acc);
-      hits += in0 && !s0.ok ? 1ull : 0ull;
+      hits += in0 && !s0.ok ? 1u : 0u;
       ro[0] = s0.next;
       if (in0) {
         s_all[tid] = ro[0].pub;
         if (!PUSH) yout[rb + tid] = ro[0].pub;
       }
     } else {
-      update_rows(S, nr, rb, P.w, PUSH ? nullptr : yout, gam, check, th_lo, th_hi, hits, acc);
+      // one row at a time: interleaving two rows (update_rows) needs more than the 64 registers
+      // a 1024-thread CTA allows next to this kernel's state and spills (4% slower on BA)
+      for (int i = tid; i < nr; i += blockDim.x) {
+        Own o = {S.yh[i], S.yl[i], S.x[i]};
+        update_one(o, dev::f2{S.vh[i], S.vl[i]}, S.sum[i], gam, check, check ? P.w[rb + i] : 0.0f, th_lo, th_hi,
+                   hits, acc);
+        S.yh[i] = o.pub;
+        S.yl[i] = o.aux;
+        S.x[i] = o.xs;
+        if (!PUSH) yout[rb + i] = o.pub;
+      }
     }
     gamma_store(gnext, T);  // visible to every thread after the next __syncthreads
     if (check && P.iterflag) write_check_partial(P, acc, slot, T);

@@ -70,6 +70,9 @@ struct RowArrays {
   float* vl;
 };
 
+// Safe-division hits are counted per thread in 32 bits (a call runs fewer than 2^31 / nblocks
+// iterations and a thread updates a few rows per iteration) and summed in 64 bits per CTA.
+
 // per-thread accumulators of the stop test
 struct CheckAcc {
   float rmax = 0.0f;
@@ -165,9 +168,9 @@ __device__ __forceinline__ void check_terms(const RowStep& r, const Own& s, cons
 }
 // the update of one row with, at a check, its stop-test terms
 __device__ __forceinline__ void update_one(Own& s, const dev::f2 v, float sn, dev::f2 gam, bool check, float wi,
-                                           float th_lo, float th_hi, unsigned long long& hits, CheckAcc& acc) {
+                                           float th_lo, float th_hi, unsigned& hits, CheckAcc& acc) {
   const RowStep r = update_core(s, v, sn, gam);
-  hits += r.ok ? 0ull : 1ull;
+  hits += r.ok ? 0u : 1u;
   if (check) check_terms(r, s, v, wi, th_lo, th_hi, acc);
   s = r.next;
 }
@@ -176,7 +179,7 @@ __device__ __forceinline__ void update_one(Own& s, const dev::f2 v, float sn, de
 // null, the new gathered values to global memory)
 __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, const float* __restrict__ w,
                                             float* __restrict__ yout, dev::f2 gam, bool check,
-                                            float th_lo, float th_hi, unsigned long long& hits,
+                                            float th_lo, float th_hi, unsigned& hits,
                                             CheckAcc& acc) {
   // rows i and i + blockDim.x together: their arithmetic has no branch between it, so the two
   // dependency chains interleave (a row past the end computes on a fixed point and stores nothing)
@@ -194,7 +197,7 @@ __device__ __forceinline__ void update_rows(const RowArrays& S, int nr, int rb, 
       check_terms(r1, s1, v1, w[rb + i], th_lo, th_hi, acc);
       if (in2) check_terms(r2, s2, v2, w[rb + i2], th_lo, th_hi, acc);
     }
-    hits += (r1.ok ? 0ull : 1ull) + (in2 && !r2.ok ? 1ull : 0ull);
+    hits += (r1.ok ? 0u : 1u) + (in2 && !r2.ok ? 1u : 0u);
     S.yh[i] = r1.next.pub;
     S.yl[i] = r1.next.aux;
     S.x[i] = r1.next.xs;

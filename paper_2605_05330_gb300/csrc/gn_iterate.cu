@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_persistent(const IterParams 
   const int nheavy = s_nheavy;
   const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
 
-  unsigned long long hits = 0;
+  unsigned hits = 0;
   int parity = 0, slot = 0, stop = 0;
   unsigned nbar = 0;
   int nchk = 0;  // checks so far (selects the check word)
