@@ -64,11 +64,15 @@ typedef enum {
 #define GN_REORDER_RCM 1        /* reverse Cuthill-McKee: locality of neighbour gathers */
 #define GN_REORDER_DEGREE 2     /* descending degree */
 
-#define GN_SYNC_AUTO 0          /* the grid barrier (GN_SYNC_GRID) */
+#define GN_SYNC_AUTO 0          /* halo mode: GN_SYNC_TAGGED; other modes: GN_SYNC_GRID */
 #define GN_SYNC_GRID 1          /* a grid-wide barrier after every iteration */
 #define GN_SYNC_NEIGHBOUR 2     /* halo mode: each CTA waits only for the CTAs whose rows it reads
                                    (per-CTA completed-iteration flags); grid-wide only at the stop
                                    test.  Same arithmetic, bit-identical results. */
+#define GN_SYNC_TAGGED 3        /* halo mode: every exchanged value carries a one-bit tag of its
+                                   iteration (three rotating buffers); a CTA polls its halo values
+                                   until their tags are the iteration's, with no barrier between
+                                   stop tests.  Same arithmetic, bit-identical results. */
 
 #define GN_KERNEL_AUTO 0
 #define GN_KERNEL_PERSISTENT 1  /* multi-CTA persistent kernel with a bounded grid barrier */
@@ -89,8 +93,10 @@ typedef struct {
                            steps (no stop test) through step kernels that keep a checkpoint
                            every ceil(sqrt(T)) steps */
   long long spin_limit; /* device wait limit in polls (0 = default 1<<22) */
-  int debug_unreachable_barrier; /* test hook: make the first grid barrier unreachable so
-                                    that every CTA hits spin_limit; must be 0 in use */
+  int debug_unreachable_barrier; /* test hook, must be 0 in use.  1: make the first grid
+                                    barrier unreachable so that every CTA hits spin_limit.
+                                    2: under GN_SYNC_TAGGED, the first halo wait expects a tag
+                                    that no value carries (other modes: as 1) */
   int resume;           /* 1: continue from the full-precision state the last gn_run left on the
                            handle (x0 ignored); with start_iter = that run's end this reproduces
                            an uninterrupted run bit for bit */

@@ -96,23 +96,128 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
+// tagged exchange: the tag bit of a halo value (its sign; every weighted state is >= +0), the
+// halo slots per thread loaded before the interior sums, and per batch after them
+constexpr unsigned kTagBit = 0x80000000u;
+constexpr int kTagPre = 2;
+constexpr int kTagBatch = 8;
+// push: the inbox is contiguous, so a thread reads four consecutive slots with one 16-byte
+// load (four 4-byte accesses, each with its own tag), kTagGroups such groups at a time (the
+// first ones issued before the interior sums)
+constexpr int kTagGroups = 4;
+
+
 // push: the send list, own states (s_all) into the other CTAs' inboxes, a warp per piece of
-// at most 128 slots; each lane's (up to four) source reads are issued together
+// at most 128 slots, lane j storing slots 4j .. 4j + 3 of the piece with one 16-byte store
+// (pieces start at multiples of 4 slots); the four ids come in one 8-byte load, and the
+// builder placed the values so that each of the four gathers reads distinct banks where it
+// could.  TAG: each value goes out with tag bit `tag` in its sign (four 4-byte relaxed
+// accesses in one vector store).
+template <bool TAG>
 __device__ __forceinline__ void push_states(const int4* __restrict__ piece, int npiece,
                                             const uint16_t* __restrict__ src, const float* __restrict__ s_all,
-                                            float* __restrict__ inbox) {
+                                            float* __restrict__ inbox, unsigned tag = 0u) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   for (int q = warp; q < npiece; q += nwarps) {
     const int4 pc = piece[q];
-    int id[4];
+    if (4 * lane < pc.y) {
+      const uint2 ids = *reinterpret_cast<const uint2*>(src + pc.z + 4 * lane);
+      const float a = s_all[ids.x & 0xffffu], b = s_all[ids.x >> 16], c = s_all[ids.y & 0xffffu],
+                  d = s_all[ids.y >> 16];
+      if (TAG) {
+        asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(
+                         reinterpret_cast<unsigned*>(inbox) + pc.x + 4 * lane),
+                     "r"((__float_as_uint(a) & ~kTagBit) | tag), "r"((__float_as_uint(b) & ~kTagBit) | tag),
+                     "r"((__float_as_uint(c) & ~kTagBit) | tag), "r"((__float_as_uint(d) & ~kTagBit) | tag)
+                     : "memory");
+      } else {
+        *reinterpret_cast<float4*>(inbox + pc.x + 4 * lane) = make_float4(a, b, c, d);
+      }
+    }
+  }
+}
+
+// tagged exchange: a halo slot's value once its tag bit is `want`, polling again until then;
+// bounded like the barriers (a limit, or another CTA's reported failure, sets `fail`); with
+// `fail` already set it returns at once
+__device__ __forceinline__ unsigned poll_tag(const unsigned* p, unsigned v, unsigned want, const IterParams& P,
+                                             bool& fail) {
+  long long spins = 0;
+  while (((v ^ want) & kTagBit) && !fail) {
+    ++spins;
+    if ((spins & 255) == 0 && dev::ld_relaxed_int(P.status) != 0) {
+      fail = true;
+    } else if (spins > P.spin_limit) {
+      atomicOr(P.status, DEV_TIMEOUT);
+      fail = true;
+    } else {
+      v = dev::ld_relaxed(p);
+    }
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
+// push, tagged: whether the slots 4q .. 4q + 3 below lx all carry tag `want`
+__device__ __forceinline__ bool ready4(uint4 v, int q, int lx, unsigned want) {
+  const int t = 4 * q;
+  const unsigned m = ((v.x ^ want) | (t + 1 < lx ? v.y ^ want : 0u) | (t + 2 < lx ? v.z ^ want : 0u) |
+                      (t + 3 < lx ? v.w ^ want : 0u));
+  return !(m & kTagBit);
+}
+
+// push, tagged: this thread's groups q = q0 + u * kThreads (u < kTagGroups) of four consecutive
+// inbox slots, v[u] already loaded once.  Every round reloads all the groups that still hold
+// a slot with another tag, together (one round trip per round), bounded like the barriers;
+// then the values, tags cleared, into the halo.
+__device__ __forceinline__ void land_tagged4(uint4 (&v)[kTagGroups], int q0, int lx, const uint4* __restrict__ src4,
+                                             float* __restrict__ s_halo, unsigned want, const IterParams& P,
+                                             bool& fail) {
+  long long spins = 0;
+  for (;;) {
+    bool done = true;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) id[u] = lane + 32 * u < pc.y ? src[pc.z + lane + 32 * u] : -1;
-    float val[4];
+    for (int u = 0; u < kTagGroups; ++u) {
+      const int q = q0 + u * kThreads;
+      if (4 * q < lx && !ready4(v[u], q, lx, want)) done = false;
+    }
+    if (done || fail) break;
+    ++spins;
+    if ((spins & 255) == 0 && dev::ld_relaxed_int(P.status) != 0) {
+      fail = true;
+      break;
+    }
+    if (spins > P.spin_limit) {
+      atomicOr(P.status, DEV_TIMEOUT);
+      fail = true;
+      break;
+    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) val[u] = id[u] >= 0 ? s_all[id[u]] : 0.0f;
+    for (int u = 0; u < kTagGroups; ++u) {
+      const int q = q0 + u * kThreads;
+      if (4 * q < lx && !ready4(v[u], q, lx, want)) v[u] = ld_relaxed_v4(src4 + q);
+    }
+  }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (id[u] >= 0) inbox[pc.x + lane + 32 * u] = val[u];
+  for (int u = 0; u < kTagGroups; ++u) {
+    const int q = q0 + u * kThreads, t = 4 * q;
+    if (t + 3 < lx) {
+      reinterpret_cast<float4*>(s_halo)[q] =
+          make_float4(__uint_as_float(v[u].x & ~kTagBit), __uint_as_float(v[u].y & ~kTagBit),
+                      __uint_as_float(v[u].z & ~kTagBit), __uint_as_float(v[u].w & ~kTagBit));
+    } else if (t < lx) {
+      s_halo[t] = __uint_as_float(v[u].x & ~kTagBit);
+      if (t + 1 < lx) s_halo[t + 1] = __uint_as_float(v[u].y & ~kTagBit);
+      if (t + 2 < lx) s_halo[t + 2] = __uint_as_float(v[u].z & ~kTagBit);
+    }
   }
 }
 
@@ -152,7 +257,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long l
 // REG: a CTA owns at most 2 * kThreads rows and each thread keeps its (at most two) rows'
 // state in registers across iterations; only y (for the neighbour sums) goes to shared memory.
 // PUSH: the halo exchange by inboxes, else pull.
-template <bool REG, bool PUSH>
+// TAG: the tagged exchange (no grid barrier between checks), else the barrier or the flags.
+template <bool REG, bool PUSH, bool TAG>
 __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TailShared T;
@@ -229,6 +335,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   const float th_lo = (float)P.theta, th_hi = (float)(1.0 - P.theta);
   const unsigned halo_bytes = (unsigned)((H.lx + 3) & ~3) * 4u;
 
+  // tagged exchange: three buffers of inbox_len slots (push: the inboxes; pull: one slot per
+  // vertex); iteration r reads buffer r % 3, whose values carry tag bit (r / 3) % 2
+  // (the buffers' base and length are re-read from the launch parameters where they are used,
+  // which keeps them out of the registers)
+#define TBUF reinterpret_cast<unsigned*>(P.inbox)
+#define TLEN ((size_t)P.inbox_len)
+  // tagged exchange state: the buffer index (bits 0..1) and the tag bit of this iteration
+  unsigned tcode = P.bad_tag ? kTagBit : 0u;
+
   unsigned hits = 0;
   int parity = 0, slot = 0, stop = 0;
   unsigned nbar = 0;
@@ -236,8 +351,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   unsigned mphase = 0;  // parity of the mbarrier phase the next copy completes
   int k = P.k_start;
 
-  // prologue: the starting states into inbox[0] (push), then every CTA's halo is complete
-  if (PUSH) push_states(piece, H.npiece, ssrc, s_all, P.inbox);
+  // prologue: the starting states into inbox[0] (push), then every CTA's halo is complete.
+  // Tagged: the starting states into buffer 0 with tag 0, and this CTA's slots of buffers 1 and
+  // 2 marked with tag 1, which their first readers (iterations 1 and 2, tag 0) do not accept.
+  if (TAG) {
+    if (PUSH) {
+      push_states<true>(piece, H.npiece, ssrc, s_all, P.inbox, 0u);
+      push_states<true>(piece, H.npiece, ssrc, s_all, P.inbox + TLEN, kTagBit);
+      push_states<true>(piece, H.npiece, ssrc, s_all, P.inbox + 2 * TLEN, kTagBit);
+    } else {
+      for (int i = tid; i < nr; i += blockDim.x) {
+        const unsigned u = __float_as_uint(s_all[i]) & ~kTagBit;
+        dev::st_relaxed_u32(TBUF + rb + i, u);
+        dev::st_relaxed_u32(TBUF + TLEN + rb + i, u | kTagBit);
+        dev::st_relaxed_u32(TBUF + 2 * TLEN + rb + i, u | kTagBit);
+      }
+    }
+  } else if (PUSH) {
+    push_states<false>(piece, H.npiece, ssrc, s_all, P.inbox);
+  }
   if (P.iterflag) {
     if (publish_and_stop(P, false, slot, false, dev::f2{0.0f, 0.0f}, k - 1, T) == 2) stop = 2;
   } else {
@@ -260,6 +392,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     float* inbox_out = PUSH ? P.inbox + (size_t)((r + 1) & 1) * (size_t)P.inbox_len : nullptr;
     const float* __restrict__ yin = parity ? P.y1 : P.y0;  // pull
     float* __restrict__ yout = parity ? P.y0 : P.y1;
+    const unsigned tbit = tcode & kTagBit;  // tagged: this iteration's tag,
+    const unsigned ocode = (tcode & 3u) == 2u ? (tcode ^ kTagBit) & kTagBit : tcode + 1u;  // and r + 1's
+    const unsigned obit = ocode & kTagBit;
+    const unsigned* tin = TBUF + (size_t)(tcode & 3u) * TLEN;
+    unsigned* tout = TBUF + (size_t)(ocode & 3u) * TLEN;
 
     // 0. neighbour synchronisation: the dependencies' iteration r - 1 (their pushes)
     if (P.iterflag && !synced) {
@@ -271,8 +408,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       __syncthreads();
       fail = !s_dep_ok;
     }
-    // 1. the halo, asynchronously
-    if (PUSH) {
+    // 1. the halo, asynchronously (tagged: each thread's first kTagPre slots, in flight during
+    // the interior sums)
+    unsigned pre[kTagPre];
+    uint4 pre4[kTagGroups];
+    if (TAG && PUSH) {
+      const uint4* src4 = reinterpret_cast<const uint4*>(tin + H.inbox_off);
+#pragma unroll
+      for (int u = 0; u < kTagGroups; ++u) {
+        const int q = tid + u * kThreads;
+        pre4[u] = 4 * q < H.lx ? ld_relaxed_v4(src4 + q) : make_uint4(0u, 0u, 0u, 0u);
+      }
+    } else if (TAG) {
+#pragma unroll
+      for (int u = 0; u < kTagPre; ++u) {
+        const int t = tid + u * kThreads;
+        pre[u] = t < H.lx ? dev::ld_relaxed(tin + xlist[t]) : 0u;
+      }
+    } else if (PUSH) {
       if (tid == 0 && H.lx > 0 && !fail) bulk_fetch(s_halo, inbox_in + H.inbox_off, halo_bytes, &s_bar);
     } else {
       for (int t = tid; t < H.lx; t += blockDim.x) cp_async4(&s_halo[t], yin + xlist[t]);
@@ -280,8 +433,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     }
     // 2. interior rows need only own values
     for (int s = warp; s < H.ns_int; s += nwarps) sum_slice(s, meta, srow, sell, s_all, S.sum);
-    // 3. boundary rows and heavy chunks after the halo has landed
-    if (PUSH) {
+    // 3. boundary rows and heavy chunks after the halo has landed.  Tagged: a slot whose tag is
+    // not yet this iteration's is polled again; the slots past the first kTagPre per thread are
+    // loaded kTagBatch at a time
+    if (TAG && PUSH) {
+      const uint4* src4 = reinterpret_cast<const uint4*>(tin + H.inbox_off);
+      land_tagged4(pre4, tid, H.lx, src4, s_halo, tbit, P, fail);
+      for (int q0 = tid + kTagGroups * kThreads; 4 * q0 < H.lx; q0 += kTagGroups * kThreads) {
+#pragma unroll
+        for (int u = 0; u < kTagGroups; ++u) {
+          const int q = q0 + u * kThreads;
+          pre4[u] = 4 * q < H.lx ? ld_relaxed_v4(src4 + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        land_tagged4(pre4, q0, H.lx, src4, s_halo, tbit, P, fail);
+      }
+    } else if (TAG) {
+#pragma unroll
+      for (int u = 0; u < kTagPre; ++u) {
+        const int t = tid + u * kThreads;
+        if (t < H.lx) s_halo[t] = __uint_as_float(poll_tag(tin + xlist[t], pre[u], tbit, P, fail) & ~kTagBit);
+      }
+      for (int t0 = tid + kTagPre * kThreads; t0 < H.lx; t0 += kTagBatch * kThreads) {
+        unsigned v[kTagBatch];
+#pragma unroll
+        for (int u = 0; u < kTagBatch; ++u) {
+          const int t = t0 + u * kThreads;
+          v[u] = t < H.lx ? dev::ld_relaxed(tin + xlist[t]) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kTagBatch; ++u) {
+          const int t = t0 + u * kThreads;
+          if (t < H.lx) s_halo[t] = __uint_as_float(poll_tag(tin + xlist[t], v[u], tbit, P, fail) & ~kTagBit);
+        }
+      }
+    }
+    if (TAG) {
+      if (__syncthreads_or(fail)) {
+        stop = 2;
+        break;
+      }
+    } else if (PUSH) {
       if (H.lx > 0 && !fail) {
         if (!mbar_wait(&s_bar, mphase, P.spin_limit)) {
           fail = true;
@@ -292,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     } else {
       asm volatile("cp.async.wait_all;" ::: "memory");
     }
-    __syncthreads();
+    if (!TAG) __syncthreads();
     {
       // one round-robin over the warps of [boundary slices | heavy chunks], as two loops (a
       // branch inside the slice loop costs the slices more than the split does)
@@ -332,7 +523,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
         ro[1] = s1.next;
         if (in1) {
           s_all[tid + kThreads] = ro[1].pub;
-          if (!PUSH) yout[rb + tid + kThreads] = ro[1].pub;
+          if (!PUSH && TAG) dev::st_relaxed_u32(tout + rb + tid + kThreads, (__float_as_uint(ro[1].pub) & ~kTagBit) | obit);
+          if (!PUSH && !TAG) yout[rb + tid + kThreads] = ro[1].pub;
         }
       } else {
         s0 = update_core(ro[0], rv[0], in0 ? S.sum[tid] : 0.0f, gam);
@@ -342,7 +534,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
       ro[0] = s0.next;
       if (in0) {
         s_all[tid] = ro[0].pub;
-        if (!PUSH) yout[rb + tid] = ro[0].pub;
+        if (!PUSH && TAG) dev::st_relaxed_u32(tout + rb + tid, (__float_as_uint(ro[0].pub) & ~kTagBit) | obit);
+        if (!PUSH && !TAG) yout[rb + tid] = ro[0].pub;
       }
     } else {
       // one row at a time: interleaving two rows (update_rows) needs more than the 64 registers
@@ -354,7 +547,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
         S.yh[i] = o.pub;
         S.yl[i] = o.aux;
         S.x[i] = o.xs;
-        if (!PUSH) yout[rb + i] = o.pub;
+        if (!PUSH && TAG) dev::st_relaxed_u32(tout + rb + i, (__float_as_uint(o.pub) & ~kTagBit) | obit);
+        if (!PUSH && !TAG) yout[rb + i] = o.pub;
       }
     }
     gamma_store(gnext, T);  // visible to every thread after the next __syncthreads
@@ -362,16 +556,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
     // 5. the new own states into the other CTAs' inboxes
     if (PUSH) {
       __syncthreads();
-      push_states(piece, H.npiece, ssrc, s_all, inbox_out);
+      if (TAG)
+        push_states<true>(piece, H.npiece, ssrc, s_all, P.inbox + (size_t)(ocode & 3u) * TLEN, obit);
+      else
+        push_states<false>(piece, H.npiece, ssrc, s_all, inbox_out);
     }
-    // 6. synchronisation and the stop decision (grid mode: at a check, fused into the barrier)
-    if (P.iterflag)
+    // 6. synchronisation and the stop decision (grid mode: at a check, fused into the barrier).
+    // Tagged, between checks: only a bar.sync (pull: the own values of this update before the
+    // next interior sums; push has one before its stores)
+    if (P.iterflag) {
       stop = publish_and_stop(P, fail, slot, check, gam, k, T);
-    else if (check)
-      stop = check_barrier(P, PUSH, fail, nbar, nchk, gam, k, acc, T);
-    else
+    } else if (check) {
+      stop = check_barrier(P, PUSH || TAG, fail, nbar, nchk, gam, k, acc, T);
+    } else if (TAG) {
+      stop = 0;
+      if (!PUSH) __syncthreads();
+    } else {
       stop = barrier_and_stop(P, PUSH, fail, nbar, slot, false, gam, k, T);
+    }
     synced = check;
+    tcode = ocode;
     if (stop == 2) break;
     parity ^= 1;
     if (stop) {
@@ -382,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   if (stop == 2) {
     // timeout: the status word says so.  A copy that this CTA started may still be in flight
     // into shared memory: wait for it (bounded) before the CTA exits; leave the state as is.
-    if (PUSH && fail && H.lx > 0) mbar_wait(&s_bar, mphase ^ 1u, P.spin_limit);
+    if (!TAG && PUSH && fail && H.lx > 0) mbar_wait(&s_bar, mphase ^ 1u, P.spin_limit);
     return;
   }
   float* yfin = parity ? P.y1 : P.y0;
@@ -401,12 +605,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gn_halo(const IterParams P) {
   } else {
     for (int i = tid; i < nr; i += blockDim.x) yfin[rb + i] = S.yh[i];
   }
+#undef TBUF
+#undef TLEN
   finish_run(P, S, rb, nr, hits, k, parity, T);
 }
 
-const void* halo_kernel(int rows_pad, bool push) {
-  if (push) return rows_pad <= 2 * kThreads ? (const void*)k_gn_halo<true, true> : (const void*)k_gn_halo<false, true>;
-  return rows_pad <= 2 * kThreads ? (const void*)k_gn_halo<true, false> : (const void*)k_gn_halo<false, false>;
+const void* halo_kernel(int rows_pad, bool push, bool tagged) {
+  const bool reg = rows_pad <= 2 * kThreads;
+  if (tagged) {
+    if (push) return reg ? (const void*)k_gn_halo<true, true, true> : (const void*)k_gn_halo<false, true, true>;
+    return reg ? (const void*)k_gn_halo<true, false, true> : (const void*)k_gn_halo<false, false, true>;
+  }
+  if (push) return reg ? (const void*)k_gn_halo<true, true, false> : (const void*)k_gn_halo<false, true, false>;
+  return reg ? (const void*)k_gn_halo<true, false, false> : (const void*)k_gn_halo<false, false, false>;
 }
 
 }  // namespace gn

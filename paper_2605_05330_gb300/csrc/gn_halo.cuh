@@ -10,14 +10,14 @@ namespace gn {
 // partition).  It changes with every change to gn_halo_build.cu that changes its output, so the
 // recorded DRAM traffic of the kernel, which depends on it, is tied to this header and not to
 // the builder's code.
-constexpr int kHaloLayoutVersion = 3;
+constexpr int kHaloLayoutVersion = 4;
 
 // header of a CTA block (int32 words), followed by 16-byte aligned sections
 struct HaloHeader {
   int ns_int;      // interior slices (every row's neighbours are own rows)
   int ns;          // all slices
   int nheavy;      // heavy rows
-  int lx;          // external halo length
+  int lx;          // external halo length (push: inbox slots, each owner's run padded to 4)
   int sell_len;    // SELL entries (with padding)
   int heavy_len;   // local ids of the heavy rows
   int zero_id;     // local id of the first of 32 zero slots, one per bank (padding)
@@ -34,8 +34,8 @@ struct HaloHeader {
   int off_hchunk;  // (entry offset into hl, count) per chunk
   int off_hpart;   // float per chunk: its sum of this iteration
   int npiece;      // send-list pieces
-  int off_piece;   // int4 per piece: (first inbox slot, length, first source, 0)
-  int off_src;     // uint16 per sent value: the own row it comes from
+  int off_piece;   // int4 per piece: (first inbox slot, length, first source, 0), multiples of 4
+  int off_src;     // uint16 per sent slot: the own row it comes from (padding: a zero slot)
   int off_x;       // pull: int32 per halo value, its vertex id
   int pad0;
 };

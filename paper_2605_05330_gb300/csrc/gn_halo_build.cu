@@ -141,7 +141,60 @@ static constexpr double kPullDensity = 4.0;
 // work runs on the host threads, a CTA at a time (parallel_items); every CTA's output is its own.
 static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
                                    const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
-                                   const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits);
+                                   bool push, size_t smem_limit, bool* fits);
+
+// Padding in a send list: the id field holds kPadSrc | bank, read as the zero slot of that bank
+// once the blocks' zero slots are placed (owner-local ids are below 32768).
+static constexpr int kPadSrc = 0xFFE0;
+
+// The slots of one send piece: m <= kSendPiece values (owner-local ids, bank = id & 31) in
+// L = round4(m) slots.  The owner's warp stores slots 4j .. 4j + 3 from lane j (one 16-byte
+// store) and gathers their values with four instructions, the u-th reading slot 4j + u of
+// every lane, so the placement decides the bank conflicts of the gathers.  Greedy, values of
+// the busiest banks first: each goes to the instruction u that has a free lane and does not
+// yet read its bank, the least loaded such u first (any u with a free lane when every one
+// reads it).  place[s] = the index of the value in slot s, or -(1 + bank) for padding, bank
+// being one that no value of that instruction reads (where there is one).  Returns L.
+static int place_piece(const int32_t* lid, int m, int* place) {
+  const int L = (m + 3) & ~3, lanes = L / 4;
+  int load[32] = {0};
+  for (int i = 0; i < m; ++i) ++load[lid[i] & 31];
+  int order[kSendPiece];
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::sort(order, order + m, [&](int a, int b) {
+    const int ba = lid[a] & 31, bb = lid[b] & 31;
+    if (load[ba] != load[bb]) return load[ba] > load[bb];
+    return ba != bb ? ba < bb : a < b;
+  });
+  int cnt[4] = {0, 0, 0, 0}, uof[kSendPiece];
+  uint32_t used[4] = {0, 0, 0, 0};
+  for (int k = 0; k < m; ++k) {
+    const int i = order[k], bk = lid[i] & 31;
+    int best = -1;
+    for (int u = 0; u < 4; ++u) {
+      if (cnt[u] >= lanes) continue;
+      if (best < 0) {
+        best = u;
+        continue;
+      }
+      const int cu = (int)(used[u] >> bk & 1u), cb = (int)(used[best] >> bk & 1u);
+      if (cu < cb || (cu == cb && cnt[u] < cnt[best])) best = u;
+    }
+    uof[i] = best;
+    ++cnt[best];
+    used[best] |= 1u << bk;
+  }
+  int pos[4] = {0, 0, 0, 0};
+  for (int i = 0; i < m; ++i) {
+    const int u = uof[i];
+    place[4 * pos[u]++ + u] = i;
+  }
+  for (int u = 0; u < 4; ++u) {
+    const int zb = used[u] == 0xffffffffu ? 0 : __builtin_ctz(~used[u]);
+    for (int j = pos[u]; j < lanes; ++j) place[4 * j + u] = -1 - zb;
+  }
+  return L;
+}
 
 gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
                      const std::vector<int32_t>& part, size_t smem_limit, int want, bool* fits) {
@@ -187,23 +240,17 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
       sectors_of[b] = sec;
     }
   });
-  std::vector<int64_t> inbox_off(nb + 1, 0);
   int64_t vals = 0, sectors = 0;
   for (int b = 0; b < nb; ++b) {
-    inbox_off[b + 1] = inbox_off[b] + (int64_t)((ext[b].size() + 3) & ~(size_t)3);
     vals += (int64_t)ext[b].size();
     sectors += sectors_of[b];
   }
   // the exchange: forced, or by the density of the halos in memory
   bool push = want == GN_GATHER_HALO_PUSH ||
               (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
-  if (push && inbox_off[nb] > (int64_t)INT32_MAX) {  // inbox slots do not fit 32 bits
-    if (want == GN_GATHER_HALO_PUSH) return GN_OK;
-    push = false;
-  }
   for (int attempt = 0; attempt < 2; ++attempt, push = !push) {
     if (attempt == 1 && want != GN_GATHER_HALO) break;
-    gn_status st = build_halo_blocks(g, rp, ci, part, ext, inbox_off, push, smem_limit, fits);
+    gn_status st = build_halo_blocks(g, rp, ci, part, ext, push, smem_limit, fits);
     if (st != GN_OK || *fits) return st;
   }
   return GN_OK;
@@ -212,7 +259,7 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
 // The blocks for one exchange (see build_halo).
 static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
                                    const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
-                                   const std::vector<int64_t>& inbox_off, bool push, size_t smem_limit, bool* fits) {
+                                   bool push, size_t smem_limit, bool* fits) {
   *fits = false;
   const int nb = (int)part.size() - 1;
   const int n = g->n;
@@ -220,27 +267,78 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
   const int R = (max_rows + 3) & ~3;
 
-  // send lists: for each owner o, the (inbox slot, own row) pairs in slot order.  The slots of
-  // consumer c come before those of c + 1, and within c's halo (sorted by id) the vertices of
-  // o are one run, found by binary search.
-  std::vector<std::vector<std::pair<int32_t, int32_t>>> sends(nb);
+  // Push: each consumer's inbox.  Consumer c's halo (ext[c], sorted by id) holds the values of
+  // one owner CTA as one run (the partition is contiguous); in the inbox each run starts at a
+  // multiple of 4 slots and is padded to one, and its pieces of kSendPiece slots are placed by
+  // place_piece.  hslot: the inbox slot (within c's region) of ext[c][t]; hsrc: c's slots in
+  // order, the owner-local id read for each (padding: kPadSrc | bank); hrun: c's runs, (owner,
+  // first slot), in owner order.  Pull: the halo in ext order, 4-slot aligned regions.
+  std::vector<std::vector<int32_t>> hslot(nb), hsrc(nb);
+  std::vector<std::vector<int2>> hrun(nb);
+  std::vector<int64_t> lxp(nb), inbox_off(nb + 1, 0);
+  if (push) {
+    parallel_items(nb, [&](int c, int) {
+      const std::vector<int32_t>& xc = ext[c];
+      std::vector<int32_t>& hs = hslot[c];
+      std::vector<int32_t>& sc = hsrc[c];
+      std::vector<int2>& runs = hrun[c];
+      hs.resize(xc.size());
+      sc.clear();
+      runs.clear();
+      int32_t lid[kSendPiece];
+      int place[kSendPiece];
+      for (size_t t = 0, o = 0; t < xc.size();) {
+        while (xc[t] >= part[o + 1]) ++o;
+        size_t e = t;
+        while (e < xc.size() && xc[e] < part[o + 1]) ++e;
+        runs.push_back(make_int2((int)o, (int)sc.size()));
+        for (size_t a = t; a < e; a += kSendPiece) {
+          const int m = (int)std::min<size_t>(kSendPiece, e - a);
+          for (int i = 0; i < m; ++i) lid[i] = xc[a + i] - part[o];
+          const int L = place_piece(lid, m, place);
+          const int base = (int)sc.size();
+          for (int q = 0; q < L; ++q) {
+            const int i = place[q];
+            if (i >= 0) {
+              sc.push_back(lid[i]);
+              hs[a + i] = base + q;
+            } else {
+              sc.push_back(kPadSrc | (-1 - i));
+            }
+          }
+        }
+        t = e;
+      }
+      lxp[c] = (int64_t)sc.size();
+    });
+  } else {
+    for (int c = 0; c < nb; ++c) lxp[c] = (int64_t)ext[c].size();
+  }
+  for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + ((lxp[c] + 3) & ~(int64_t)3);
+  if (inbox_off[nb] > (int64_t)INT32_MAX) return GN_OK;  // inbox slots do not fit 32 bits
+
+  // send lists: for each owner o, its run in every consumer's inbox (binary search in the
+  // consumer's runs), cut into pieces of kSendPiece slots from the run's start (place_piece's
+  // pieces), and the source id of every slot
+  struct Sends {
+    std::vector<int4> pieces;  // (first inbox slot, length, first source, 0), all multiples of 4
+    std::vector<uint16_t> src;
+  };
+  std::vector<Sends> sends(nb);
   if (push) {
     parallel_items(nb, [&](int o, int) {
-      std::vector<std::pair<size_t, size_t>> run(nb);  // o's run in each consumer's halo
-      size_t total = 0;
+      Sends& so = sends[o];
       for (int c = 0; c < nb; ++c) {
-        const std::vector<int32_t>& xc = ext[c];
-        const size_t t0 = std::lower_bound(xc.begin(), xc.end(), part[o]) - xc.begin();
-        const size_t t1 = std::lower_bound(xc.begin() + t0, xc.end(), part[o + 1]) - xc.begin();
-        run[c] = {t0, t1};
-        total += t1 - t0;
+        const std::vector<int2>& runs = hrun[c];
+        const auto it = std::lower_bound(runs.begin(), runs.end(), o, [](const int2& r, int v) { return r.x < v; });
+        if (it == runs.end() || it->x != o) continue;
+        const int s0 = it->y, s1 = it + 1 == runs.end() ? (int)lxp[c] : (it + 1)->y;
+        for (int a = s0; a < s1; a += kSendPiece) {
+          const int len = std::min(kSendPiece, s1 - a);
+          so.pieces.push_back(make_int4((int)(inbox_off[c] + a), len, (int)so.src.size(), 0));
+          for (int q = a; q < a + len; ++q) so.src.push_back((uint16_t)hsrc[c][q]);
+        }
       }
-      std::vector<std::pair<int32_t, int32_t>>& so = sends[o];
-      so.resize(total);
-      size_t at = 0;
-      for (int c = 0; c < nb; ++c)
-        for (size_t t = run[c].first; t < run[c].second; ++t)
-          so[at++] = {(int32_t)(inbox_off[c] + (int64_t)t), ext[c][t] - part[o]};
     });
   }
 
@@ -293,7 +391,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       H.ns_int = ns_int;
       H.ns = ns;
       H.nheavy = (int)heavy.size();
-      H.lx = (int)xb.size();
+      H.lx = (int)lxp[b];
       H.ndep = (int)dep.size();
       H.inbox_off = (int)inbox_off[b];
       std::vector<int2> meta(ns);
@@ -333,16 +431,8 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       H.sell_len = sell_len;
       H.heavy_len = heavy_len;
       H.nchunk = (int)hchunk.size() / 2;
-      // send pieces: runs of consecutive inbox slots, at most kSendPiece long
-      const std::vector<std::pair<int32_t, int32_t>>& sd = sends[b];
-      std::vector<int4> pieces;
-      std::vector<uint16_t> src(sd.size());
-      for (size_t e = 0; e < sd.size(); ++e) {
-        src[e] = (uint16_t)sd[e].second;
-        if (pieces.empty() || pieces.back().y == kSendPiece || sd[e].first != pieces.back().x + pieces.back().y)
-          pieces.push_back(make_int4(sd[e].first, 0, (int)e, 0));
-        ++pieces.back().y;
-      }
+      std::vector<int4> pieces = std::move(sends[b].pieces);
+      std::vector<uint16_t> src = std::move(sends[b].src);
       H.npiece = (int)pieces.size();
       size_t off = align16(sizeof(HaloHeader));
       H.off_meta = (int)off;
@@ -382,7 +472,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   int lx_max = 0;
   size_t blk_max = 0;
   for (int b = 0; b < nb; ++b) {
-    lx_max = std::max(lx_max, (int)ext[b].size());
+    lx_max = std::max(lx_max, plans[b].H.lx);
     blk_max = std::max(blk_max, (size_t)plans[b].H.bytes);
   }
   const int Lp = (lx_max + 3) & ~3;
@@ -436,7 +526,12 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       }
       HaloHeader* H = reinterpret_cast<HaloHeader*>(B);
       H->zero_id = zero_id;
-      for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = (int32_t)t;
+      for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = push ? hslot[b][t] : (int32_t)t;
+      if (push) {  // the padding of the send list reads the zero slot of the bank it names
+        uint16_t* sp = reinterpret_cast<uint16_t*>(B + H->off_src);
+        for (size_t e = 0; e < plans[b].src.size(); ++e)
+          if (sp[e] >= kPadSrc) sp[e] = (uint16_t)(zero_id + (((sp[e] & 31) - zero_id) & 31));
+      }
       auto lid = [&](int j) -> uint16_t {
         return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
       };
@@ -533,11 +628,12 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   });
   GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
   GN_CUDA(cudaMalloc(&g->d_hblob, blob_bytes));
-  if (push) {
-    g->inbox_len = std::max<int64_t>(inbox_off[nb], 4);
-    GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 2 * (size_t)g->inbox_len));
-    GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 2 * (size_t)g->inbox_len, g->stream));
-  }
+  // the exchange buffers: push, the inboxes; pull, one slot per vertex (read by the tagged
+  // exchange only); three of each (two alternate under the barrier or the flags, three rotate
+  // in the tagged exchange)
+  g->inbox_len = push ? std::max<int64_t>(inbox_off[nb], 4) : (int64_t)((n + 3) & ~3);
+  GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 3 * (size_t)g->inbox_len));
+  GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 3 * (size_t)g->inbox_len, g->stream));
   g->halo_push = push;
   GN_CUDA(cudaMemcpyAsync(g->d_hoff, hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, g->stream));
   GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.get(), blob_bytes, cudaMemcpyHostToDevice, g->stream));

@@ -94,7 +94,8 @@ struct gn_graph {
   gn::CheckPartial* d_partials = nullptr;  // [2][nblocks]
   unsigned* d_bar = nullptr;   // [8]: grid-barrier counter, then three 64-bit check words (bytes 8..31)
   unsigned* d_iterflag = nullptr;  // [kFlagStride * nblocks] per-CTA push counts (halo mode)
-  float* d_inbox = nullptr;        // [2][inbox_len] halo inboxes (halo mode, push exchange)
+  float* d_inbox = nullptr;        // [3][inbox_len] halo exchange buffers (halo mode): push, the
+                                   // inboxes; pull, a slot per vertex for the tagged exchange
   bool halo_push = false;          // halo mode: push exchange (else pull)
   int64_t inbox_len = 0;
   gn::DevInfo* d_info = nullptr;

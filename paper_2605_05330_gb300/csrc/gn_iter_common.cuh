@@ -48,7 +48,9 @@ struct IterParams {
   int halo_pad;
   long long spin_limit;
   int unreachable;
-  // halo mode: two inbox buffers of inbox_len floats (the per-CTA halo exchange)
+  int bad_tag;  // test hook (tagged exchange): the first halo wait expects a tag no value carries
+  // halo mode: three exchange buffers of inbox_len floats (push: the per-CTA inboxes, of which
+  // the barrier and the flags use two; pull: a slot per vertex, for the tagged exchange)
   float* inbox;
   long long inbox_len;
   // neighbour synchronisation (halo mode): iterflag[kFlagStride * b] counts the pushes CTA b

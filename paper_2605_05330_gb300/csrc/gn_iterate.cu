@@ -32,7 +32,7 @@ enum GatherMode : int {
 
 gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
                      const std::vector<int32_t>& part, size_t smem_limit, int want, bool* fits);  // gn_halo.cu
-const void* halo_kernel(int rows_pad, bool push);
+const void* halo_kernel(int rows_pad, bool push, bool tagged);
 
 // The generic persistent kernel: values gathered through L1/L2 (MODE_GMEM, MODE_SMEM_CSR),
 // G lanes per light row and a warp per heavy row.
@@ -279,9 +279,14 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
   if (halo_fits) {
     g->mode = MODE_HALO;
     g->gather = GN_GATHER_HALO;
-    const void* hk = halo_kernel(g->rows_pad_halo, g->halo_push);
+    const void* hk = halo_kernel(g->rows_pad_halo, g->halo_push, false);
+    const void* hkt = halo_kernel(g->rows_pad_halo, g->halo_push, true);
     GN_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    GN_CUDA(cudaFuncSetAttribute(hkt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit));
+    int per_sm_t = 0;
     GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (KernelFn)hk, kThreads, g->smem_bytes));
+    GN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_t, (KernelFn)hkt, kThreads, g->smem_bytes));
+    per_sm = std::min(per_sm, per_sm_t);
   } else {
     if (want == GN_GATHER_SMEM_CSR && csr_s > kSmemLimit)
       return fail(GN_ERR_TOO_LARGE, "gn_create: the CSR-in-shared-memory mode does not fit");
@@ -389,7 +394,9 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   P.heavy = g->heavy;
   P.rows_pad = g->mode == MODE_HALO ? g->rows_pad_halo : ((g->max_rows + 3) & ~3);
   P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
-  P.unreachable = p.debug_unreachable_barrier ? 1 : 0;
+  const bool tagged = g->mode == MODE_HALO && (p.sync == GN_SYNC_TAGGED || p.sync == GN_SYNC_AUTO);
+  P.unreachable = p.debug_unreachable_barrier != 0 && !(tagged && p.debug_unreachable_barrier == 2) ? 1 : 0;
+  P.bad_tag = tagged && p.debug_unreachable_barrier == 2 ? 1 : 0;
   P.iterflag = (g->mode == MODE_HALO && p.sync == GN_SYNC_NEIGHBOUR) ? g->d_iterflag : nullptr;
   P.inbox = g->d_inbox;
   P.inbox_len = g->inbox_len;
@@ -409,7 +416,7 @@ gn_status run_iterations(gn_graph* g, int k_start, int k_end, double tol, const 
   GN_LAUNCHED();
   P.gtab = (const float2*)g->d_gtab;
   P.gtab_len = glen;
-  KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo, g->halo_push)
+  KernelFn fn = g->mode == MODE_HALO ? (KernelFn)halo_kernel(g->rows_pad_halo, g->halo_push, tagged)
                                      : pick_kernel(g->group, g->mode);
   GN_CUDA(cudaMemsetAsync(g->d_bar, 0, sizeof(unsigned) * 8, g->stream));  // counter and check words
   if (P.iterflag)
@@ -474,7 +481,7 @@ extern "C" gn_status gn_run(gn_graph* g, const float* x0, int max_iters, double 
       !std::isfinite(p.gamma0) || !std::isfinite(p.gamma1) || p.gamma1 < 0 || p.gamma0 < 0 ||
       (p.gamma_mode != GN_GAMMA_PURSUIT && p.gamma_mode != GN_GAMMA_FIXED) ||
       p.kernel < GN_KERNEL_AUTO || p.kernel > GN_KERNEL_CTA || p.sync < GN_SYNC_AUTO ||
-      p.sync > GN_SYNC_NEIGHBOUR)
+      p.sync > GN_SYNC_TAGGED)
     return fail(GN_ERR_ARG, "gn_run: bad argument");
   GN_CUDA(cudaSetDevice(g->device));
   GN_CUDA(cudaMemsetAsync(g->d_info, 0, sizeof(DevInfo), g->stream));
@@ -862,6 +869,7 @@ extern "C" gn_status gn_run_noalloc(int32_t n, const int32_t* row_ptr, const int
     P.rows_pad = R;
     P.spin_limit = p.spin_limit > 0 ? p.spin_limit : (1ll << 22);
     P.unreachable = p.debug_unreachable_barrier ? 1 : 0;
+    P.bad_tag = 0;
     void* args[] = {(void*)&P};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = info != nullptr;

@@ -27,7 +27,7 @@ HOST, DEVICE = 0, 1
 GAMMA_PURSUIT, GAMMA_FIXED = 0, 1
 REORDER_NONE, REORDER_RCM, REORDER_DEGREE = 0, 1, 2
 KERNEL_AUTO, KERNEL_PERSISTENT, KERNEL_CTA = 0, 1, 2
-SYNC_AUTO, SYNC_GRID, SYNC_NEIGHBOUR = 0, 1, 2
+SYNC_AUTO, SYNC_GRID, SYNC_NEIGHBOUR, SYNC_TAGGED = 0, 1, 2, 3
 GATHER_AUTO, GATHER_GLOBAL, GATHER_SMEM_CSR, GATHER_HALO = 0, 1, 2, 3
 GATHER_HALO_PULL, GATHER_HALO_PUSH = 4, 5
 EXCHANGE_NAMES = {0: "none", 1: "pull", 2: "push"}

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2605_05330_gb300 import inputs
-from tests.test_gpu_parity import assert_close_rel, fixed_steps
+from tests.test_gpu_parity import K_ITERATE, assert_close_rel, fixed_steps
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def split(x, vtx):
     return [np.asarray(x[vtx[i]:vtx[i + 1]]) for i in range(len(vtx) - 1)]
 
 
-@pytest.mark.parametrize("k", [1, 5, 20])
+@pytest.mark.parametrize("k", [1, 5, K_ITERATE])
 def test_batch_iterates_match_oracle(gn, k):
     specs = small_specs()
     b = gn.Batch(batch_items(specs))
@@ -202,12 +202,12 @@ def test_assignment_up_to_k96_in_one_launch(gn):
         specs.append(("assignment", k, w, (2.0 - w.astype(np.float64)).reshape(k, k)))
     specs.append(inputs.er_graph(3000, 10.0, 4010))
     b = gn.Batch(batch_items(specs))
-    run_kw, pk = fixed_steps(20)
+    run_kw, pk = fixed_steps(K_ITERATE)
     x, infos = b.run(params=gn.default_params(**pk), **run_kw)
     for s, xi, inf in zip(specs, split(x, b.vtx_off), infos):
         inst = as_csr(s)
         xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, p=oracle.params(**pk), **run_kw)
-        assert inf["iters"] == 20
+        assert inf["iters"] == K_ITERATE
         assert_close_rel(xi, xo)
     x, infos = b.run(max_iters=2000, tol=1e-7)
     for s, xi, inf in zip(specs, split(x, b.vtx_off), infos):

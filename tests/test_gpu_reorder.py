@@ -110,11 +110,11 @@ def test_rcm_order_matches_definition(gn, case):
 def test_rcm_handle_runs_like_the_oracle(gn):
     """The device-searched order changes only the internal layout: the run follows the oracle."""
     import oracle
-    from tests.test_gpu_parity import assert_close_rel, fixed_steps, to_np
+    from tests.test_gpu_parity import K_ITERATE, assert_close_rel, fixed_steps, to_np
     inst = _islands()
     g = gn.Graph(inst.row_ptr, inst.col_idx, inst.w, reorder=gn.REORDER_RCM)
     assert g.vertex_order_source() == "device"
-    run_kw, pk = fixed_steps(20)
+    run_kw, pk = fixed_steps(K_ITERATE)
     x, info = g.run(params=gn.default_params(**pk), **run_kw)
     xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, p=oracle.params(**pk), **run_kw)
     assert_close_rel(to_np(x), xo)

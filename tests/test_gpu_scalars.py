@@ -24,7 +24,7 @@ import pytest
 
 import oracle
 from paper_2605_05330_gb300 import inputs
-from tests.test_gpu_parity import FLOOR, GATHERS, REL, _tie_free, assert_close_rel, dev_graph, fixed_steps, to_np
+from tests.test_gpu_parity import FLOOR, GATHERS, K_ITERATE, REL, _tie_free, assert_close_rel, dev_graph, fixed_steps, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def _d_x(inst, gamma, x):
 
 
 @pytest.mark.parametrize("gather", ["halo", "global"])
-@pytest.mark.parametrize("k", [1, 5, 20])
+@pytest.mark.parametrize("k", [1, 5, K_ITERATE])
 @pytest.mark.parametrize("which", list(INSTANCES))
 def test_reported_scalars_match_oracle(gn, which, k, gather):
     inst = INSTANCES[which]()
