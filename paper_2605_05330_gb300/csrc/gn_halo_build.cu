@@ -157,32 +157,43 @@ static constexpr int kPadSrc = 0xFFE0;
 // being one that no value of that instruction reads (where there is one).  Returns L.
 static int place_piece(const int32_t* lid, int m, int* place) {
   const int L = (m + 3) & ~3, lanes = L / 4;
+  // the values bucketed by bank (a counting sort), the banks by decreasing load (ties by bank)
   int load[32] = {0};
   for (int i = 0; i < m; ++i) ++load[lid[i] & 31];
-  int order[kSendPiece];
-  for (int i = 0; i < m; ++i) order[i] = i;
-  std::sort(order, order + m, [&](int a, int b) {
-    const int ba = lid[a] & 31, bb = lid[b] & 31;
-    if (load[ba] != load[bb]) return load[ba] > load[bb];
-    return ba != bb ? ba < bb : a < b;
-  });
+  int at[32], first[32], bucket[kSendPiece];
+  for (int b = 0, a = 0; b < 32; ++b) {
+    first[b] = at[b] = a;
+    a += load[b];
+  }
+  for (int i = 0; i < m; ++i) bucket[at[lid[i] & 31]++] = i;
+  int border[32];
+  for (int b = 0; b < 32; ++b) {  // insertion sort: stable, so equal loads keep bank order
+    int j = b;
+    while (j > 0 && load[border[j - 1]] < load[b]) {
+      border[j] = border[j - 1];
+      --j;
+    }
+    border[j] = b;
+  }
   int cnt[4] = {0, 0, 0, 0}, uof[kSendPiece];
   uint32_t used[4] = {0, 0, 0, 0};
-  for (int k = 0; k < m; ++k) {
-    const int i = order[k], bk = lid[i] & 31;
-    int best = -1;
-    for (int u = 0; u < 4; ++u) {
-      if (cnt[u] >= lanes) continue;
-      if (best < 0) {
-        best = u;
-        continue;
+  for (int r = 0; r < 32 && load[border[r]] > 0; ++r) {
+    const int bk = border[r];
+    for (int k = first[bk]; k < first[bk] + load[bk]; ++k) {
+      int best = -1;
+      for (int u = 0; u < 4; ++u) {
+        if (cnt[u] >= lanes) continue;
+        if (best < 0) {
+          best = u;
+          continue;
+        }
+        const int cu = (int)(used[u] >> bk & 1u), cb = (int)(used[best] >> bk & 1u);
+        if (cu < cb || (cu == cb && cnt[u] < cnt[best])) best = u;
       }
-      const int cu = (int)(used[u] >> bk & 1u), cb = (int)(used[best] >> bk & 1u);
-      if (cu < cb || (cu == cb && cnt[u] < cnt[best])) best = u;
+      uof[bucket[k]] = best;
+      ++cnt[best];
+      used[best] |= 1u << bk;
     }
-    uof[i] = best;
-    ++cnt[best];
-    used[best] |= 1u << bk;
   }
   int pos[4] = {0, 0, 0, 0};
   for (int i = 0; i < m; ++i) {
@@ -284,6 +295,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       std::vector<int2>& runs = hrun[c];
       hs.resize(xc.size());
       sc.clear();
+      sc.reserve(xc.size() + xc.size() / 2 + 64);
       runs.clear();
       int32_t lid[kSendPiece];
       int place[kSendPiece];
