@@ -130,6 +130,78 @@ static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int
   }
 }
 
+// color_slice for up to 64 colours, on fixed-size arrays: the same edges in the same order, the
+// same choices, so the same columns.  lid[l][0 .. nl[l]) lists lane l's ids; col[l][k] receives
+// the column of lid[l][k].
+struct ColorScratch64 {
+  int16_t at_l[32 * 64], at_b[32 * 64];  // [vertex * W + colour] -> edge, or -1 (built on demand)
+  uint8_t elane[32 * 64], ebank[32 * 64], ecol[32 * 64];
+  int16_t path[32 * 64];
+};
+static void color_slice64(int W, const uint16_t (*lid)[64], const int* nl, uint8_t (*col)[64], ColorScratch64& cs) {
+  const uint64_t mask = W == 64 ? ~0ull : (1ull << W) - 1;
+  uint64_t ul[32] = {0}, ub[32] = {0};
+  bool tables = false;
+  auto put = [&](int f, int x) {
+    cs.ecol[f] = (uint8_t)x;
+    ul[cs.elane[f]] |= 1ull << x;
+    ub[cs.ebank[f]] |= 1ull << x;
+    if (tables) {
+      cs.at_l[cs.elane[f] * W + x] = (int16_t)f;
+      cs.at_b[cs.ebank[f] * W + x] = (int16_t)f;
+    }
+  };
+  int e = 0;
+  for (int l = 0; l < 32; ++l) {
+    for (int k = 0; k < nl[l]; ++k, ++e) {
+      const int b = lid[l][k] & 31;
+      cs.elane[e] = (uint8_t)l;
+      cs.ebank[e] = (uint8_t)b;
+      const uint64_t both = ~(ul[l] | ub[b]) & mask;
+      int a;
+      if (both) {
+        a = __builtin_ctzll(both);
+      } else {
+        if (!tables) {
+          for (int i = 0; i < 32 * W; ++i) cs.at_l[i] = cs.at_b[i] = -1;
+          for (int f = 0; f < e; ++f) {
+            cs.at_l[cs.elane[f] * W + cs.ecol[f]] = (int16_t)f;
+            cs.at_b[cs.ebank[f] * W + cs.ecol[f]] = (int16_t)f;
+          }
+          tables = true;
+        }
+        a = __builtin_ctzll(~ul[l]);
+        const int c = __builtin_ctzll(~ub[b]);
+        int np = 0, v = b, cur = a;
+        bool bank_side = true;
+        for (;;) {
+          const int f = bank_side ? cs.at_b[v * W + cur] : cs.at_l[v * W + cur];
+          if (f < 0) break;
+          cs.path[np++] = (int16_t)f;
+          v = bank_side ? cs.elane[f] : cs.ebank[f];
+          bank_side = !bank_side;
+          cur = cur == a ? c : a;
+        }
+        for (int q = 0; q < np; ++q) {  // the path's edges give up their colours
+          const int f = cs.path[q], x = cs.ecol[f];
+          cs.at_l[cs.elane[f] * W + x] = -1;
+          cs.at_b[cs.ebank[f] * W + x] = -1;
+          ul[cs.elane[f]] &= ~(1ull << x);
+          ub[cs.ebank[f]] &= ~(1ull << x);
+        }
+        for (int q = 0; q < np; ++q) {
+          const int f = cs.path[q];
+          put(f, cs.ecol[f] == a ? c : a);
+        }
+      }
+      put(e, a);
+    }
+  }
+  e = 0;
+  for (int l = 0; l < 32; ++l)
+    for (int k = 0; k < nl[l]; ++k) col[l][k] = cs.ecol[e++];
+}
+
 // A CTA's halo is "dense" when it averages at least this many values per 32-byte sector:
 // then the pull exchange reads few sectors and wins; below it the push exchange does.
 static constexpr double kPullDensity = 4.0;
@@ -387,12 +459,18 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
         for (int64_t e = a; e < c && !bnd; ++e) bnd = (ci[e] < rb || ci[e] >= re);
         (bnd ? light_bnd : light_int).push_back(r);
       }
-      auto by_deg = [&](int x, int y) {
-        const int dx = rp[rb + x + 1] - rp[rb + x], dy = rp[rb + y + 1] - rp[rb + y];
-        return dx != dy ? dx > dy : x < y;
+      // by degree, descending, then by row (the lists are in row order and light degrees are at
+      // most kHeavyHalo, so a stable counting sort)
+      auto by_deg = [&](std::vector<int>& v) {
+        int at[kHeavyHalo + 2] = {0};
+        for (int r : v) ++at[kHeavyHalo - (int)(rp[rb + r + 1] - rp[rb + r]) + 1];
+        for (int d = 1; d <= kHeavyHalo + 1; ++d) at[d] += at[d - 1];
+        std::vector<int> out(v.size());
+        for (int r : v) out[at[kHeavyHalo - (int)(rp[rb + r + 1] - rp[rb + r])]++] = r;
+        v.swap(out);
       };
-      std::sort(light_int.begin(), light_int.end(), by_deg);
-      std::sort(light_bnd.begin(), light_bnd.end(), by_deg);
+      by_deg(light_int);
+      by_deg(light_bnd);
       // interior-only slices first; the rest (the interior tail + boundary rows) after
       const int ns_int = (int)light_int.size() / 32;
       std::vector<int> order(light_int.begin(), light_int.end());
@@ -504,8 +582,14 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     std::vector<uint16_t> lids[32];
     std::vector<int> cols[32];
     ColorScratch cs;
-    std::vector<int> occ;
     std::vector<uint16_t> bucket[32];
+    // a slice on fixed-size arrays (every light row has at most kHeavyHalo = 64 entries)
+    uint16_t lidA[32][64];
+    int nl[32];
+    uint8_t colA[32][64];
+    int occ[32 * 64];
+    uint16_t fold[32 * 64];
+    ColorScratch64 cs64;
   };
   std::vector<EncodeScratch> scratch(host_threads());
   parallel_items(nb, [&](int b, int t) {
@@ -515,7 +599,11 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     std::vector<uint16_t>* lids = X.lids;
     std::vector<int>* cols = X.cols;
     ColorScratch& cs = X.cs;
-    std::vector<int>& occ = X.occ;
+    int* occ = X.occ;
+    uint16_t(*lidA)[64] = X.lidA;
+    int* nl = X.nl;
+    uint8_t(*colA)[64] = X.colA;
+    uint16_t* fold = X.fold;
     uint64_t usedcols[32];
     std::vector<uint16_t>* bucket = X.bucket;
     {
@@ -554,41 +642,70 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       // that each column's real entries lie in distinct banks, then pad each lane's empty
       // columns with the zero slot of a bank no real entry of that column uses (all padding of
       // a column reads that one address: a broadcast).
+      static_assert(kHeavyHalo <= 64, "a light row's entries fit one 64-bit column set");
       for (int s = 0; s < H->ns; ++s) {
         const int W = meta[s].y;
+        int load[32] = {0};
         for (int l = 0; l < 32; ++l) {
           const int r = srow[s * 32 + l];
-          lids[l].clear();
+          int m = 0;
           if (r >= 0)
-            for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) lids[l].push_back(lid(ci[e]));
+            for (int64_t e = rp[rb + r]; e < rp[rb + r + 1]; ++e) {
+              const uint16_t id = lid(ci[e]);
+              lidA[l][m++] = id;
+              ++load[id & 31];
+            }
+          nl[l] = m;
         }
         // colours for the slice's busiest bank; when that is more than the slice's width, the
         // colours past the width fold into each lane's free columns, least-used bank first
         // (only those gathers can conflict)
-        int Wc = W, load[32] = {0};
-        for (int l = 0; l < 32; ++l)
-          for (uint16_t id : lids[l]) ++load[id & 31];
+        int Wc = W;
         for (int t = 0; t < 32; ++t) Wc = std::max(Wc, load[t]);
-        color_slice(Wc, lids, cols, cs);
-        if (Wc > W) {
-          occ.assign(32 * (size_t)W, 0);  // occ[bank * W + column]
+        if (Wc <= 64) {
+          color_slice64(Wc, lidA, nl, colA, X.cs64);
+        } else {  // more than 64 colours: the general version
+          for (int l = 0; l < 32; ++l) lids[l].assign(lidA[l], lidA[l] + nl[l]);
+          color_slice(Wc, lids, cols, cs);
           for (int l = 0; l < 32; ++l)
-            for (size_t t = 0; t < lids[l].size(); ++t)
-              if (cols[l][t] < W) ++occ[(lids[l][t] & 31) * W + cols[l][t]];
+            for (int k = 0; k < nl[l]; ++k) colA[l][k] = (uint8_t)std::min(cols[l][k], 255);
+        }
+        if (Wc > W) {
+          // occ[bank * W + column] counts the real entries below the width, fresh[bank] holds the
+          // columns the bank does not use yet, used[l] lane l's columns; one pass over the
+          // entries, which also lists those to fold (lane order, then entry order).  A folded
+          // entry takes the free column of its lane that its bank uses least, lowest first: the
+          // lowest free column in fresh when there is one, else a scan of the counts.
+          const uint64_t wmask = W == 64 ? ~0ull : (1ull << W) - 1;
+          for (int t = 0; t < 32 * W; ++t) occ[t] = 0;
+          uint64_t fresh[32], used[32];
+          int nfold = 0;
+          for (int t = 0; t < 32; ++t) fresh[t] = wmask;
           for (int l = 0; l < 32; ++l) {
-            uint64_t used = 0;
-            for (size_t t = 0; t < lids[l].size(); ++t)
-              if (cols[l][t] < W) used |= 1ull << cols[l][t];
-            for (size_t t = 0; t < lids[l].size(); ++t) {
-              if (cols[l][t] < W) continue;
-              const int bk = lids[l][t] & 31;
-              int best = -1;
-              for (int k = 0; k < W; ++k)
-                if (!(used >> k & 1ull) && (best < 0 || occ[bk * W + k] < occ[bk * W + best])) best = k;
-              cols[l][t] = best;
-              used |= 1ull << best;
-              ++occ[bk * W + best];
+            uint64_t u = 0;
+            for (int k = 0; k < nl[l]; ++k) {
+              const int c = colA[l][k], bk = lidA[l][k] & 31;
+              if (c < W) {
+                ++occ[bk * W + c];
+                fresh[bk] &= ~(1ull << c);
+                u |= 1ull << c;
+              } else {
+                fold[nfold++] = (uint16_t)(l * 64 + k);
+              }
             }
+            used[l] = u;
+          }
+          for (int q = 0; q < nfold; ++q) {
+            const int l = fold[q] >> 6, k = fold[q] & 63, bk = lidA[l][k] & 31;
+            const uint64_t cand = ~used[l] & fresh[bk] & wmask;
+            int best = cand ? __builtin_ctzll(cand) : -1;
+            if (best < 0)
+              for (int c = 0; c < W; ++c)
+                if (!(used[l] >> c & 1ull) && (best < 0 || occ[bk * W + c] < occ[bk * W + best])) best = c;
+            colA[l][k] = (uint8_t)best;
+            used[l] |= 1ull << best;
+            ++occ[bk * W + best];
+            fresh[bk] &= ~(1ull << best);
           }
         }
         // the real entries, each lane's used columns and each column's used banks; then the
@@ -598,11 +715,11 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
         const int base = meta[s].x;
         for (int l = 0; l < 32; ++l) {
           uint64_t used = 0;
-          for (size_t t = 0; t < lids[l].size(); ++t) {
-            const int k = cols[l][t];
-            sell[base + (k >> 2) * 128 + l * 4 + (k & 3)] = lids[l][t];
+          for (int t = 0; t < nl[l]; ++t) {
+            const int k = colA[l][t];
+            sell[base + (k >> 2) * 128 + l * 4 + (k & 3)] = lidA[l][t];
             used |= 1ull << k;
-            colbanks[k] |= 1u << (lids[l][t] & 31);
+            colbanks[k] |= 1u << (lidA[l][t] & 31);
           }
           usedcols[l] = used;
         }
