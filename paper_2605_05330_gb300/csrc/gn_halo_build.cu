@@ -229,7 +229,8 @@ static constexpr int kPadSrc = 0xFFE0;
 // being one that no value of that instruction reads (where there is one).  Returns L.
 static int place_piece(const int32_t* lid, int m, int* place) {
   const int L = (m + 3) & ~3, lanes = L / 4;
-  // the values bucketed by bank (a counting sort), the banks by decreasing load (ties by bank)
+  // the values bucketed by bank (a counting sort), the banks by decreasing load, ties by bank
+  // (a counting sort of the banks by load)
   int load[32] = {0};
   for (int i = 0; i < m; ++i) ++load[lid[i] & 31];
   int at[32], first[32], bucket[kSendPiece];
@@ -238,29 +239,24 @@ static int place_piece(const int32_t* lid, int m, int* place) {
     a += load[b];
   }
   for (int i = 0; i < m; ++i) bucket[at[lid[i] & 31]++] = i;
-  int border[32];
-  for (int b = 0; b < 32; ++b) {  // insertion sort: stable, so equal loads keep bank order
-    int j = b;
-    while (j > 0 && load[border[j - 1]] < load[b]) {
-      border[j] = border[j - 1];
-      --j;
-    }
-    border[j] = b;
-  }
+  int nat[kSendPiece + 2] = {0}, border[32];
+  for (int b = 0; b < 32; ++b) ++nat[kSendPiece - load[b] + 1];
+  for (int v = 1; v <= kSendPiece + 1; ++v) nat[v] += nat[v - 1];
+  for (int b = 0; b < 32; ++b) border[nat[kSendPiece - load[b]]++] = b;
+  // each value to the gather u with a free lane that least clashes with its bank, then the least
+  // loaded, then the lowest: the smallest score (capacity, clash, count, u)
   int cnt[4] = {0, 0, 0, 0}, uof[kSendPiece];
   uint32_t used[4] = {0, 0, 0, 0};
   for (int r = 0; r < 32 && load[border[r]] > 0; ++r) {
     const int bk = border[r];
     for (int k = first[bk]; k < first[bk] + load[bk]; ++k) {
-      int best = -1;
+      int best = 0, bs = INT_MAX;
       for (int u = 0; u < 4; ++u) {
-        if (cnt[u] >= lanes) continue;
-        if (best < 0) {
+        const int sc = (cnt[u] >= lanes ? (1 << 30) : 0) + (int)((used[u] >> bk & 1u) << 20) + cnt[u] * 4 + u;
+        if (sc < bs) {
+          bs = sc;
           best = u;
-          continue;
         }
-        const int cu = (int)(used[u] >> bk & 1u), cb = (int)(used[best] >> bk & 1u);
-        if (cu < cb || (cu == cb && cnt[u] < cnt[best])) best = u;
       }
       uof[bucket[k]] = best;
       ++cnt[best];
@@ -307,17 +303,18 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
       std::vector<int32_t>& xb = ext[b];
       size_t count = 0;
       for (int wd = wlo; wd <= whi; ++wd) count += (size_t)__builtin_popcountll(bits[wd]);
-      xb.reserve(count);
-      int64_t sec = 0, last = -1;
+      xb.resize(count);
+      int32_t* out = xb.data();
+      // a sector is 8 vertices, one byte of the bitmap: the sectors touched are its nonzero bytes
+      constexpr uint64_t k7f = 0x7f7f7f7f7f7f7f7full;
+      int64_t sec = 0;
       for (int wd = wlo; wd <= whi; ++wd) {
         uint64_t m = bits[wd];
         bits[wd] = 0;
+        sec += __builtin_popcountll((((m & k7f) + k7f) | m) & ~k7f);
         while (m) {
-          const int j = wd * 64 + __builtin_ctzll(m);
+          *out++ = wd * 64 + __builtin_ctzll(m);
           m &= m - 1;
-          xb.push_back(j);
-          sec += (j / 8 != last);
-          last = j / 8;
         }
       }
       sectors_of[b] = sec;
