@@ -132,15 +132,16 @@ static void color_slice(int W, const std::vector<uint16_t>* lid, std::vector<int
 
 // color_slice for up to 64 colours, on fixed-size arrays: the same edges in the same order, the
 // same choices, so the same columns.  lid[l][0 .. nl[l]) lists lane l's ids; col[l][k] receives
-// the column of lid[l][k].
+// the column of lid[l][k]; ul[l] and ub[b] receive the colours used at lane l and at bank b.
 struct ColorScratch64 {
   int16_t at_l[32 * 64], at_b[32 * 64];  // [vertex * W + colour] -> edge, or -1 (built on demand)
   uint8_t elane[32 * 64], ebank[32 * 64], ecol[32 * 64];
   int16_t path[32 * 64];
 };
-static void color_slice64(int W, const uint16_t (*lid)[64], const int* nl, uint8_t (*col)[64], ColorScratch64& cs) {
+static void color_slice64(int W, const uint16_t (*lid)[64], const int* nl, uint8_t (*col)[64], ColorScratch64& cs,
+                          uint64_t* ul, uint64_t* ub) {
   const uint64_t mask = W == 64 ? ~0ull : (1ull << W) - 1;
-  uint64_t ul[32] = {0}, ub[32] = {0};
+  for (int i = 0; i < 32; ++i) ul[i] = ub[i] = 0;
   bool tables = false;
   auto put = [&](int f, int x) {
     cs.ecol[f] = (uint8_t)x;
@@ -584,11 +585,12 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     uint16_t lidA[32][64];
     int nl[32];
     uint8_t colA[32][64];
-    int occ[32 * 64];
+    uint8_t extra[32 * 64];  // per (bank, column): folded entries placed there (zero between slices)
     uint16_t fold[32 * 64];
     ColorScratch64 cs64;
   };
   std::vector<EncodeScratch> scratch(host_threads());
+  for (EncodeScratch& X : scratch) memset(X.extra, 0, sizeof X.extra);
   parallel_items(nb, [&](int b, int t) {
     EncodeScratch& X = scratch[t];
     if (!X.extpos) X.extpos.reset(new int32_t[std::max(n, 1)]);
@@ -596,7 +598,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
     std::vector<uint16_t>* lids = X.lids;
     std::vector<int>* cols = X.cols;
     ColorScratch& cs = X.cs;
-    int* occ = X.occ;
+    uint8_t* extra = X.extra;
     uint16_t(*lidA)[64] = X.lidA;
     int* nl = X.nl;
     uint8_t(*colA)[64] = X.colA;
@@ -659,51 +661,64 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
         // (only those gathers can conflict)
         int Wc = W;
         for (int t = 0; t < 32; ++t) Wc = std::max(Wc, load[t]);
+        uint64_t ul[32], ub[32];
+        const uint64_t wmask = W == 64 ? ~0ull : (1ull << W) - 1;
+        uint32_t foldlanes = 0;  // the lanes with a colour from W up
         if (Wc <= 64) {
-          color_slice64(Wc, lidA, nl, colA, X.cs64);
+          color_slice64(Wc, lidA, nl, colA, X.cs64, ul, ub);
+          for (int l = 0; l < 32; ++l) foldlanes |= (ul[l] & ~wmask) ? 1u << l : 0u;
         } else {  // more than 64 colours: the general version
           for (int l = 0; l < 32; ++l) lids[l].assign(lidA[l], lidA[l] + nl[l]);
           color_slice(Wc, lids, cols, cs);
+          for (int l = 0; l < 32; ++l) ul[l] = ub[l] = 0;
           for (int l = 0; l < 32; ++l)
-            for (int k = 0; k < nl[l]; ++k) colA[l][k] = (uint8_t)std::min(cols[l][k], 255);
-        }
-        if (Wc > W) {
-          // occ[bank * W + column] counts the real entries below the width, fresh[bank] holds the
-          // columns the bank does not use yet, used[l] lane l's columns; one pass over the
-          // entries, which also lists those to fold (lane order, then entry order).  A folded
-          // entry takes the free column of its lane that its bank uses least, lowest first: the
-          // lowest free column in fresh when there is one, else a scan of the counts.
-          const uint64_t wmask = W == 64 ? ~0ull : (1ull << W) - 1;
-          for (int t = 0; t < 32 * W; ++t) occ[t] = 0;
-          uint64_t fresh[32], used[32];
-          int nfold = 0;
-          for (int t = 0; t < 32; ++t) fresh[t] = wmask;
-          for (int l = 0; l < 32; ++l) {
-            uint64_t u = 0;
             for (int k = 0; k < nl[l]; ++k) {
-              const int c = colA[l][k], bk = lidA[l][k] & 31;
-              if (c < W) {
-                ++occ[bk * W + c];
-                fresh[bk] &= ~(1ull << c);
-                u |= 1ull << c;
-              } else {
-                fold[nfold++] = (uint16_t)(l * 64 + k);
+              colA[l][k] = (uint8_t)std::min(cols[l][k], 255);
+              if (cols[l][k] >= W) foldlanes |= 1u << l;
+              if (cols[l][k] < 64) {  // colours from 64 up are all folded below (W <= 64)
+                ul[l] |= 1ull << cols[l][k];
+                ub[lidA[l][k] & 31] |= 1ull << cols[l][k];
               }
             }
-            used[l] = u;
+        }
+        if (Wc > W) {
+          // The colouring is proper, so below the width bank bk holds column c at most once: the
+          // bit c of ub[bk].  A folded entry (colour from W up; lane order, then entry order)
+          // takes the free column of its lane that its bank uses least, lowest first: the lowest
+          // free column its bank does not use when there is one (bit sets), else a scan of the
+          // counts (the bit plus the folded entries already placed there, in extra).
+          uint64_t fresh[32], used[32];
+          for (int t = 0; t < 32; ++t) {
+            fresh[t] = ~ub[t] & wmask;
+            used[t] = ul[t] & wmask;
+          }
+          int nfold = 0;
+          for (int l = 0; l < 32; ++l) {
+            if (!(foldlanes >> l & 1u)) continue;  // nothing of lane l to fold
+            for (int k = 0; k < nl[l]; ++k)
+              if (colA[l][k] >= W) fold[nfold++] = (uint16_t)(l * 64 + k);
           }
           for (int q = 0; q < nfold; ++q) {
             const int l = fold[q] >> 6, k = fold[q] & 63, bk = lidA[l][k] & 31;
             const uint64_t cand = ~used[l] & fresh[bk] & wmask;
             int best = cand ? __builtin_ctzll(cand) : -1;
-            if (best < 0)
-              for (int c = 0; c < W; ++c)
-                if (!(used[l] >> c & 1ull) && (best < 0 || occ[bk * W + c] < occ[bk * W + best])) best = c;
+            if (best < 0) {
+              int bo = INT_MAX;
+              for (int c = 0; c < W; ++c) {
+                if (used[l] >> c & 1ull) continue;
+                const int o = (int)(ub[bk] >> c & 1ull) + extra[bk * 64 + c];
+                if (o < bo) {
+                  bo = o;
+                  best = c;
+                }
+              }
+            }
             colA[l][k] = (uint8_t)best;
             used[l] |= 1ull << best;
-            ++occ[bk * W + best];
             fresh[bk] &= ~(1ull << best);
+            ++extra[bk * 64 + best];
           }
+          for (int q = 0; q < nfold; ++q) extra[(lidA[fold[q] >> 6][fold[q] & 63] & 31) * 64 + colA[fold[q] >> 6][fold[q] & 63]] = 0;
         }
         // the real entries, each lane's used columns and each column's used banks; then the
         // padding: an empty slot of column k reads the zero slot of the lowest bank no real entry
