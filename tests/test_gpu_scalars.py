@@ -242,3 +242,53 @@ def test_deep_decay_follows_oracle(gn, which):
     xb, infos = b.run(max_iters=2000, tol=1e-7, params=gn.default_params(**p))
     assert infos[0]["safe_div_hits"] == io["safe_div_hits"] and infos[0]["iters"] == io["iters"]
     np.testing.assert_array_equal(np.asarray(xb) > 0.5, set_o.astype(bool))
+
+
+@pytest.mark.parametrize("which", ["udg20k_rcm", "ba20k_s1295", "er3k_s2011"])
+def test_host_pipeline_through_the_c_abi(gn, which):
+    """The path a caller with host data takes (the one the end-to-end bench times): gn_create
+    from host CSR buffers, gn_run to a binary state with the default synchronisation, the state
+    back in a host buffer, gn_extract_is into host buffers, gn_destroy, without the binding's
+    classes.  Against the oracle's run to the same stop: the same iteration count and safe-division
+    hits, an independent set (checked by the oracle) and, on a tie-free instance, the oracle's
+    set and weight."""
+    inst, reorder = {"udg20k_rcm": lambda: (inputs.unit_disk_graph(20000, 100000, 1294), 1),
+                     "ba20k_s1295": lambda: (inputs.ba_graph(20000, 5, 1295), 0),
+                     "er3k_s2011": lambda: (inputs.er_graph(3000, 9.0, 2011), 0)}[which]()
+    L, P = _abi(gn)
+    rp = np.ascontiguousarray(inst.row_ptr, np.int32)
+    ci = np.ascontiguousarray(inst.col_idx, np.int32)
+    w = np.ascontiguousarray(inst.w, np.float32)
+    h = P()
+    st = L.gn_create(ctypes.byref(h), inst.n, rp.ctypes.data_as(P), ci.ctypes.data_as(P), w.ctypes.data_as(P),
+                     gn.HOST, reorder, None)
+    assert st == 0, L.gn_last_error()
+    try:
+        x = np.empty(inst.n, np.float32)
+        info = gn.RunInfo()
+        p = gn.default_params()
+        st = L.gn_run(h, None, 2000, 1e-7, ctypes.byref(p), 0, x.ctypes.data_as(P), ctypes.byref(info))
+        assert st == 0, L.gn_last_error()
+        mask = np.empty(inst.n, np.uint8)
+        members = np.empty(inst.n, np.int32)
+        cnt = ctypes.c_int32()
+        wt = ctypes.c_double()
+        st = L.gn_extract_is(h, None, mask.ctypes.data_as(P), members.ctypes.data_as(P),
+                             ctypes.cast(ctypes.pointer(cnt), P), ctypes.cast(ctypes.pointer(wt), P))
+        assert st >= 0, L.gn_last_error()
+    finally:
+        L.gn_destroy(h)
+    po = oracle.params(check_every=10)  # the library's default cadence of the stop test
+    xo, io = oracle.run(inst.row_ptr, inst.col_idx, inst.w, max_iters=2000, tol=1e-7, p=po)
+    assert info.iters == io["iters"]
+    assert info.safe_div_hits == io["safe_div_hits"]
+    # the GPU's set, judged by the oracle's exact check of the same state
+    sto, masko_of_gpu, _, wo_of_gpu = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, x.astype(np.float64))
+    assert sto in ("OK", "WARN_NOT_MAXIMAL")
+    np.testing.assert_array_equal(mask.astype(bool), np.asarray(masko_of_gpu).astype(bool))
+    assert sorted(members[:cnt.value].tolist()) == np.nonzero(mask)[0].tolist()
+    assert abs(wt.value - wo_of_gpu) <= 1e-12 * max(1.0, wo_of_gpu)
+    if _tie_free(inst, po):
+        _, masko, _, wo = oracle.extract_is(inst.row_ptr, inst.col_idx, inst.w, xo)
+        np.testing.assert_array_equal(mask.astype(bool), np.asarray(masko).astype(bool))
+        assert abs(wt.value - wo) <= 1e-9 * wo
