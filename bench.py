@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / multi-start / ... forms")
+    ap.add_argument("--forms", default="batched,multi_start,differentiable,warm_start",
+                    help="comma-separated forms to run beside plain GN (default: all four)")
     ap.add_argument("--warm-train", type=int, default=480,
                     help="training graphs of the learned warm start (the form's network)")
     ap.add_argument("--only", choices=["udg", "ba"], default=None,
@@ -753,11 +755,16 @@ def main():
 
     forms = None
     if rank == 0 and not args.no_forms and not args.only:
-        forms = {"batched": form_batched(gn, torch, args.steps, max(1, args.warmup)),
-                 "multi_start": form_multi_start(gn, torch),
-                 "differentiable": form_differentiable(gn, torch)}
+        want = {f.strip() for f in args.forms.split(",") if f.strip()}
+        forms = {}
+        if "batched" in want:
+            forms["batched"] = form_batched(gn, torch, args.steps, max(1, args.warmup))
+        if "multi_start" in want:
+            forms["multi_start"] = form_multi_start(gn, torch)
+        if "differentiable" in want:
+            forms["differentiable"] = form_differentiable(gn, torch)
         ui = [i for i, inst in enumerate(insts) if inst.meta["kind"] == "udg"]
-        if ui:
+        if ui and "warm_start" in want:
             forms["warm_start"] = form_warm_start(gn, torch, graphs[ui[0]], insts[ui[0]], train_graphs=args.warm_train)
 
     cpu = None
