@@ -351,77 +351,93 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   // Push: each consumer's inbox.  Consumer c's halo (ext[c], sorted by id) holds the values of
   // one owner CTA as one run (the partition is contiguous); in the inbox each run starts at a
   // multiple of 4 slots and is padded to one, and its pieces of kSendPiece slots are placed by
-  // place_piece.  hslot: the inbox slot (within c's region) of ext[c][t]; hsrc: c's slots in
-  // order, the owner-local id read for each (padding: kPadSrc | bank); hrun: c's runs, (owner,
-  // first slot), in owner order.  Pull: the halo in ext order, 4-slot aligned regions.
-  std::vector<std::vector<int32_t>> hslot(nb), hsrc(nb);
-  std::vector<std::vector<int2>> hrun(nb);
+  // place_piece.  The owner o sends its runs consumer by consumer: a piece (first inbox slot,
+  // length, first source, 0) per kSendPiece slots from each run's start, and the source id of
+  // every slot (the owner-local id read, or for padding kPadSrc | bank).  hslot: the inbox slot
+  // (within c's region) of ext[c][t].  Pull: the halo in ext order, 4-slot aligned regions.
+  struct Sends {
+    std::vector<int4> pieces;  // all four fields multiples of 4 (but the last)
+    std::vector<uint16_t> src;
+  };
+  std::vector<Sends> sends(nb);
+  std::vector<std::vector<int32_t>> hslot(nb);
   std::vector<int64_t> lxp(nb), inbox_off(nb + 1, 0);
   if (push) {
+    // each consumer's runs, (owner, padded length) in owner order
+    std::vector<std::vector<int2>> hrun(nb);
     parallel_items(nb, [&](int c, int) {
       const std::vector<int32_t>& xc = ext[c];
-      std::vector<int32_t>& hs = hslot[c];
-      std::vector<int32_t>& sc = hsrc[c];
       std::vector<int2>& runs = hrun[c];
-      hs.resize(xc.size());
-      sc.clear();
-      sc.reserve(xc.size() + xc.size() / 2 + 64);
       runs.clear();
-      int32_t lid[kSendPiece];
-      int place[kSendPiece];
+      int64_t total = 0;
       for (size_t t = 0, o = 0; t < xc.size();) {
         while (xc[t] >= part[o + 1]) ++o;
         size_t e = t;
         while (e < xc.size() && xc[e] < part[o + 1]) ++e;
-        runs.push_back(make_int2((int)o, (int)sc.size()));
+        const int len = (int)((e - t + 3) & ~(size_t)3);
+        runs.push_back(make_int2((int)o, len));
+        total += len;
+        t = e;
+      }
+      lxp[c] = total;
+    });
+    for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + lxp[c];
+    if (inbox_off[nb] > (int64_t)INT32_MAX) return GN_OK;  // inbox slots do not fit 32 bits
+    // where each run goes in its owner's lists: consumers in order
+    std::vector<std::vector<int2>> roff(nb);  // per consumer and run: (first source, first piece)
+    std::vector<int64_t> scount(nb, 0), pcount(nb, 0);
+    for (int c = 0; c < nb; ++c) {
+      roff[c].resize(hrun[c].size());
+      for (size_t j = 0; j < hrun[c].size(); ++j) {
+        const int o = hrun[c][j].x, len = hrun[c][j].y;
+        roff[c][j] = make_int2((int)scount[o], (int)pcount[o]);
+        scount[o] += len;
+        pcount[o] += (len + kSendPiece - 1) / kSendPiece;
+      }
+    }
+    for (int o = 0; o < nb; ++o) {
+      sends[o].src.resize(scount[o]);
+      sends[o].pieces.resize(pcount[o]);
+    }
+    // the placement, written straight into the owners' lists (disjoint ranges per consumer)
+    parallel_items(nb, [&](int c, int) {
+      const std::vector<int32_t>& xc = ext[c];
+      std::vector<int32_t>& hs = hslot[c];
+      hs.resize(xc.size());
+      int32_t lid[kSendPiece];
+      int place[kSendPiece];
+      int slot = 0;
+      size_t j = 0;
+      for (size_t t = 0, o = 0; t < xc.size(); ++j) {
+        while (xc[t] >= part[o + 1]) ++o;
+        size_t e = t;
+        while (e < xc.size() && xc[e] < part[o + 1]) ++e;
+        Sends& so = sends[o];
+        int soff = roff[c][j].x, poff = roff[c][j].y;
         for (size_t a = t; a < e; a += kSendPiece) {
           const int m = (int)std::min<size_t>(kSendPiece, e - a);
           for (int i = 0; i < m; ++i) lid[i] = xc[a + i] - part[o];
           const int L = place_piece(lid, m, place);
-          const int base = (int)sc.size();
+          so.pieces[poff++] = make_int4((int)(inbox_off[c] + slot), L, soff, 0);
+          uint16_t* sp = so.src.data() + soff;
           for (int q = 0; q < L; ++q) {
             const int i = place[q];
             if (i >= 0) {
-              sc.push_back(lid[i]);
-              hs[a + i] = base + q;
+              sp[q] = (uint16_t)lid[i];
+              hs[a + i] = slot + q;
             } else {
-              sc.push_back(kPadSrc | (-1 - i));
+              sp[q] = (uint16_t)(kPadSrc | (-1 - i));
             }
           }
+          slot += L;
+          soff += L;
         }
         t = e;
       }
-      lxp[c] = (int64_t)sc.size();
     });
   } else {
     for (int c = 0; c < nb; ++c) lxp[c] = (int64_t)ext[c].size();
-  }
-  for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + ((lxp[c] + 3) & ~(int64_t)3);
-  if (inbox_off[nb] > (int64_t)INT32_MAX) return GN_OK;  // inbox slots do not fit 32 bits
-
-  // send lists: for each owner o, its run in every consumer's inbox (binary search in the
-  // consumer's runs), cut into pieces of kSendPiece slots from the run's start (place_piece's
-  // pieces), and the source id of every slot
-  struct Sends {
-    std::vector<int4> pieces;  // (first inbox slot, length, first source, 0), all multiples of 4
-    std::vector<uint16_t> src;
-  };
-  std::vector<Sends> sends(nb);
-  if (push) {
-    parallel_items(nb, [&](int o, int) {
-      Sends& so = sends[o];
-      for (int c = 0; c < nb; ++c) {
-        const std::vector<int2>& runs = hrun[c];
-        const auto it = std::lower_bound(runs.begin(), runs.end(), o, [](const int2& r, int v) { return r.x < v; });
-        if (it == runs.end() || it->x != o) continue;
-        const int s0 = it->y, s1 = it + 1 == runs.end() ? (int)lxp[c] : (it + 1)->y;
-        for (int a = s0; a < s1; a += kSendPiece) {
-          const int len = std::min(kSendPiece, s1 - a);
-          so.pieces.push_back(make_int4((int)(inbox_off[c] + a), len, (int)so.src.size(), 0));
-          for (int q = a; q < a + len; ++q) so.src.push_back((uint16_t)hsrc[c][q]);
-        }
-      }
-    });
+    for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + ((lxp[c] + 3) & ~(int64_t)3);
   }
 
   // pass 1, per CTA: rows into interior / boundary / heavy, slices, chunks, send pieces and
