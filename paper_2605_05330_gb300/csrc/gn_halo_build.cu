@@ -700,12 +700,14 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
         if (Wc > W) {
           // The colouring is proper, so below the width bank bk holds column c at most once: the
           // bit c of ub[bk].  A folded entry (colour from W up; lane order, then entry order)
-          // takes the free column of its lane that its bank uses least, lowest first: the lowest
-          // free column its bank does not use when there is one (bit sets), else a scan of the
+          // takes the free column of its lane that its bank uses least, lowest first.  The
+          // columns a bank uses no time (fresh) and exactly once (once) are bit sets, so the
+          // lowest candidate comes from one of them; only columns used twice or more need the
           // counts (the bit plus the folded entries already placed there, in extra).
-          uint64_t fresh[32], used[32];
+          uint64_t fresh[32], once[32], used[32];
           for (int t = 0; t < 32; ++t) {
             fresh[t] = ~ub[t] & wmask;
+            once[t] = ub[t] & wmask;
             used[t] = ul[t] & wmask;
           }
           int nfold = 0;
@@ -716,12 +718,17 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
           }
           for (int q = 0; q < nfold; ++q) {
             const int l = fold[q] >> 6, k = fold[q] & 63, bk = lidA[l][k] & 31;
-            const uint64_t cand = ~used[l] & fresh[bk] & wmask;
-            int best = cand ? __builtin_ctzll(cand) : -1;
-            if (best < 0) {
+            const uint64_t freecols = ~used[l] & wmask;
+            int best;
+            if (freecols & fresh[bk]) {
+              best = __builtin_ctzll(freecols & fresh[bk]);
+            } else if (freecols & once[bk]) {
+              best = __builtin_ctzll(freecols & once[bk]);
+            } else {
+              best = -1;
               int bo = INT_MAX;
               for (int c = 0; c < W; ++c) {
-                if (used[l] >> c & 1ull) continue;
+                if (!(freecols >> c & 1ull)) continue;
                 const int o = (int)(ub[bk] >> c & 1ull) + extra[bk * 64 + c];
                 if (o < bo) {
                   bo = o;
@@ -729,9 +736,15 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
                 }
               }
             }
+            const uint64_t bit = 1ull << best;
             colA[l][k] = (uint8_t)best;
-            used[l] |= 1ull << best;
-            fresh[bk] &= ~(1ull << best);
+            used[l] |= bit;
+            if (fresh[bk] & bit) {  // 0 -> 1
+              fresh[bk] &= ~bit;
+              once[bk] |= bit;
+            } else {  // 1 -> 2, or more
+              once[bk] &= ~bit;
+            }
             ++extra[bk * 64 + best];
           }
           for (int q = 0; q < nfold; ++q) extra[(lidA[fold[q] >> 6][fold[q] & 63] & 31) * 64 + colA[fold[q] >> 6][fold[q] & 63]] = 0;
