@@ -541,12 +541,14 @@ def form_differentiable(gn, torch, reps=3):
 def form_warm_start(gn, torch, graph, inst, reps=3, train_graphs=48):
     """Learned warm start on the 1M-edge unit-disk graph.  The message-passing network is trained
     on GN's converged states of `train_graphs` smaller unit-disk graphs (n in [5k, 50k], same
-    density).  On four validation graphs (n = 50k) two starts choose their schedule the same way,
-    the fewest mean iterations to binary among the choices within 0.1% of the paper-schedule cold
-    start on every graph: the cold start 1/(deg+1) (schedule only) and the network's start
-    (blend and schedule).  Then on the workload graph: iterations, time to a binary state (network
-    inference included) and objective gap for plain GN (the paper's schedule), the tuned cold
-    start, the network's start, and the cold start on the network's schedule (the ablation)."""
+    density); three networks from three seeds (training is deterministic per seed).  On four
+    validation graphs (n = 50k) the starts choose their schedule the same way, the fewest mean
+    iterations to binary among the choices within 0.1% of the paper-schedule cold start on every
+    graph: the cold start 1/(deg+1) (schedule only) and each network's start (blend and
+    schedule).  Then on the workload graph: iterations, time to a binary state (network inference
+    included) and objective gap for plain GN (the paper's schedule), the tuned cold start, each
+    network's start and the cold start on its schedule (the ablation).  The headline is the
+    network with the median time."""
     from paper_2605_05330_gb300 import warmstart as ws
     t0 = time.perf_counter()
     train = ws.training_graphs(train_graphs, seed=9100, n_lo=5000, n_hi=50000,
@@ -558,21 +560,27 @@ def form_warm_start(gn, torch, graph, inst, reps=3, train_graphs=48):
         t, _ = ws.label(g)
         data.append((g, t))
     t_label = time.perf_counter() - t0 - t_gen
-    net = ws.WarmStartNet(seed=7)
-    hist = ws.train(net, data, epochs=30, lr=3e-3)
+    # three networks from three seeds: training is deterministic per seed, but iterations to
+    # binary are an erratic function of the start, so the form reports the median network
+    seeds = (7, 8, 9)
+    nets, hists = [], []
+    for sd in seeds:
+        net = ws.WarmStartNet(seed=sd)
+        hists.append(ws.train(net, data, epochs=30, lr=3e-3))
+        nets.append(net)
     for g, _ in data:
         g.close()
     t_train = time.perf_counter() - t0 - t_gen - t_label
     vals = ws.validation_graphs(4)
-    best = ws.pick_schedule(net, vals)
+    picks = [ws.pick_schedule(net, vals) for net in nets]
     best_cold = ws.pick_schedule(None, vals)
     for g in vals:
         g.close()
     select_s = time.perf_counter() - t0 - t_gen - t_label - t_train
-    if best is None or best_cold is None:
-        net.close()
+    if best_cold is None or any(b is None for b in picks):
+        for net in nets:
+            net.close()
         return {"graph": inst.name, "status": "no choice within 0.1% on the validation graphs"}
-    a, g0, T, _ = best
     _, c0, cT, _ = best_cold
 
     def timed(fn):
@@ -588,26 +596,36 @@ def form_warm_start(gn, torch, graph, inst, reps=3, train_graphs=48):
 
     t_plain, (pi, Wp) = timed(lambda: ws.run_from(graph, None, 0.9, 1000))
     t_cold, (ci, Wc) = timed(lambda: ws.run_from(graph, None, c0, cT))
-    t_warm, (wi, Ww) = timed(lambda: ws.run_from(graph, net.predict(graph, a), g0, T))
-    t_pred, _ = timed(lambda: net.predict(graph, a))
-    _, (ai, Wa) = timed(lambda: ws.run_from(graph, None, g0, T))
-    net.close()
+    runs = []
+    for sd, net, (a, g0, T, _) in zip(seeds, nets, picks):
+        t_warm, (wi, Ww) = timed(lambda: ws.run_from(graph, net.predict(graph, a), g0, T))
+        t_pred, _ = timed(lambda: net.predict(graph, a))
+        _, (ai, Wa) = timed(lambda: ws.run_from(graph, None, g0, T))
+        runs.append({"seed": sd, "alpha": a, "schedule": {"gamma0": g0, "ramp_iters": T}, "iters": wi["iters"],
+                     "time_to_binary_ms": 1000 * t_warm, "network_inference_ms": 1000 * t_pred,
+                     "objective_gap": (Wp - Ww) / Wp, "status": wi["status"],
+                     "cold_on_this_schedule": {"iters": ai["iters"], "objective_gap": (Wp - Wa) / Wp}})
+    for net in nets:
+        net.close()
+    med = sorted(runs, key=lambda r: (r["time_to_binary_ms"], r["seed"]))[len(runs) // 2]
     n_train = sum(tr.n for tr in train)
     return {"graph": inst.name,
             "training": f"{train_graphs} unit-disk graphs n in [5k,50k] ({n_train} labelled vertices), avg deg 10, "
-                        f"30 epochs, Adam 3e-3",
+                        f"30 epochs, Adam 3e-3; {len(seeds)} networks (seeds {', '.join(map(str, seeds))}), "
+                        f"deterministic training",
             "training_s": {"generate": t_gen, "label": t_label, "train": t_train, "select": select_s},
-            "bce_first_last_epoch": [hist[0], hist[-1]],
+            "bce_first_last_epoch": [hists[0][0], hists[0][-1]],
             "plain_gn": {"schedule": {"gamma0": 0.9, "ramp_iters": 1000}, "iters": pi["iters"],
                          "time_to_binary_ms": 1000 * t_plain},
             "cold_tuned": {"schedule": {"gamma0": c0, "ramp_iters": cT}, "iters": ci["iters"],
                            "time_to_binary_ms": 1000 * t_cold, "objective_gap": (Wp - Wc) / Wp},
-            "warm": {"alpha": a, "schedule": {"gamma0": g0, "ramp_iters": T}, "iters": wi["iters"],
-                     "time_to_binary_ms": 1000 * t_warm, "network_inference_ms": 1000 * t_pred,
-                     "objective_gap": (Wp - Ww) / Wp, "status": wi["status"]},
-            "cold_on_warm_schedule": {"iters": ai["iters"], "objective_gap": (Wp - Wa) / Wp},
-            "speedup_vs_plain_gn": t_plain / t_warm,
-            "speedup_vs_tuned_cold_start": t_cold / t_warm}
+            "warm": dict((k, v) for k, v in med.items() if k != "cold_on_this_schedule"),
+            "warm_note": "the network with the median time to binary of the three",
+            "cold_on_warm_schedule": med["cold_on_this_schedule"],
+            "per_seed": runs,
+            "speedup_vs_plain_gn": t_plain / (med["time_to_binary_ms"] / 1000),
+            "speedup_vs_tuned_cold_start": t_cold / (med["time_to_binary_ms"] / 1000),
+            "speedup_vs_tuned_cold_start_per_seed": [t_cold / (r["time_to_binary_ms"] / 1000) for r in runs]}
 
 
 def main():

@@ -327,11 +327,13 @@ __global__ void __launch_bounds__(256) k_dense_bwd_data(int n, const float* dHou
   }
 }
 
-// weight gradients: dWs += dZ^T H, dWn += dZ^T M, db += sum dZ over this CTA's rows
+// weight gradients over this CTA's rows: dWs = dZ^T H, dWn = dZ^T M, db = sum dZ, into the CTA's
+// own slot of part (k_reduce_parts adds the slots in CTA order, so the sum does not depend on
+// the CTAs' timing)
 template <int DIN>
 __global__ void __launch_bounds__(256) k_dense_bwd_weight(int n, int rows_per_cta, const float* __restrict__ dZ,
                                                           const float* __restrict__ H, const float* __restrict__ M,
-                                                          float* __restrict__ dW) {
+                                                          float* __restrict__ part) {
   __shared__ float sG[kRows][kH + 1];
   __shared__ float sX[kRows][2 * DIN + 1];
   const int rbeg = blockIdx.x * rows_per_cta, rend = min(n, rbeg + rows_per_cta);
@@ -370,8 +372,17 @@ __global__ void __launch_bounds__(256) k_dense_bwd_weight(int n, int rows_per_ct
 #pragma unroll
   for (int q = 0; q < (NW + 255) / 256; ++q) {
     const int p = threadIdx.x + q * 256;
-    if (p < NW) atomicAdd(&dW[p], acc[q]);
+    if (p < NW) part[(size_t)blockIdx.x * NW + p] = acc[q];
   }
+}
+
+// out[p] += sum over slots b < nslot of part[b * width + p], in slot order
+__global__ void k_reduce_parts(int nslot, int width, const float* __restrict__ part, float* __restrict__ out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= width) return;
+  float s = 0.0f;
+  for (int b = 0; b < nslot; ++b) s += part[(size_t)b * width + p];
+  out[p] += s;
 }
 
 // head: q = wo . h + bo, p = sigmoid(q); BCE loss (stable form) and dq = (p - t) / n; x0 out.
@@ -430,25 +441,24 @@ __global__ void __launch_bounds__(kHeadRows) k_head(int n, const float* __restri
   }
 }
 
-// head backward: dH3 = dq wo, dwo += dq h, dbo += dq
+// head backward: dH3 = dq wo; this CTA's rows' dwo = sum dq h and dbo = sum dq, summed in row
+// order into the CTA's slot of part (k_reduce_parts adds the slots in CTA order)
 __global__ void k_head_bwd(int n, const float* __restrict__ H, const __nv_bfloat16* __restrict__ wo_b,
-                           const float* __restrict__ dq, float* __restrict__ dH, float* __restrict__ dwo) {
+                           const float* __restrict__ dq, float* __restrict__ dH, float* __restrict__ part) {
   __shared__ float swo[kH];
-  __shared__ float sacc[kH + 1];
   for (int t = threadIdx.x; t < kH; t += blockDim.x) swo[t] = __bfloat162float(wo_b[t]);
-  for (int t = threadIdx.x; t <= kH; t += blockDim.x) sacc[t] = 0.0f;
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = blockIdx.x * blockDim.x, i = i0 + threadIdx.x;
   if (i < n) {
     const float g = dq[i];
-    for (int k = 0; k < kH; ++k) {
-      dH[(size_t)i * kH + k] = g * swo[k];
-      atomicAdd(&sacc[k], g * H[(size_t)i * kH + k]);
-    }
-    atomicAdd(&sacc[kH], g);
+    for (int k = 0; k < kH; ++k) dH[(size_t)i * kH + k] = g * swo[k];
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t <= kH; t += blockDim.x) atomicAdd(&dwo[t], sacc[t]);
+  if (threadIdx.x <= kH) {
+    const int k = threadIdx.x, i1 = min(n, i0 + (int)blockDim.x);
+    float a = 0.0f;
+    for (int r = i0; r < i1; ++r) a = fmaf(dq[r], k < kH ? H[(size_t)r * kH + k] : 1.0f, a);
+    part[(size_t)blockIdx.x * (kH + 1) + k] = a;
+  }
 }
 
 // Adam on the FP32 masters; the bf16 copy used by the kernels is refreshed
@@ -502,6 +512,7 @@ struct gn_mpnn {
   float* bufA = nullptr;            // [n x kH] scratch for gradients
   float* bufB = nullptr;
   float* bufC = nullptr;
+  float* part = nullptr;            // per-CTA partial gradients, reduced in CTA order
   double* d_loss = nullptr;
   double* h_loss = nullptr;         // pinned
   const gn_graph* last_graph = nullptr;
@@ -509,9 +520,11 @@ struct gn_mpnn {
 
 namespace gn {
 
+static unsigned blk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
 static gn_status mpnn_reserve(gn_mpnn* m, int n) {
   if (n <= m->cap) return GN_OK;
-  float** bufs[] = {&m->X, &m->dq, &m->tgt, &m->bufA, &m->bufB, &m->bufC};
+  float** bufs[] = {&m->X, &m->dq, &m->tgt, &m->bufA, &m->bufB, &m->bufC, &m->part};
   for (float** b : bufs)
     if (*b) cudaFree(*b), *b = nullptr;
   for (int l = 0; l < kL; ++l) {
@@ -527,6 +540,10 @@ static gn_status mpnn_reserve(gn_mpnn* m, int n) {
   GN_CUDA(cudaMalloc(&m->bufA, nh));
   GN_CUDA(cudaMalloc(&m->bufB, nh));
   GN_CUDA(cudaMalloc(&m->bufC, nh));
+  {  // the weight gradients' partials: a slot of the widest layer's size per 256 rows
+    constexpr int kNWmax = 2 * kH * (kF > kH ? kF : kH) + kH;
+    GN_CUDA(cudaMalloc(&m->part, sizeof(float) * (size_t)blk(n, 256) * kNWmax));
+  }
   for (int l = 0; l < kL; ++l) {
     GN_CUDA(cudaMalloc(&m->Ms[l], sizeof(float) * (size_t)n * layer_in(l)));
     GN_CUDA(cudaMalloc(&m->Zs[l], nh));
@@ -536,7 +553,6 @@ static gn_status mpnn_reserve(gn_mpnn* m, int n) {
   return GN_OK;
 }
 
-static unsigned blk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace gn
 
@@ -546,7 +562,8 @@ extern "C" void gn_mpnn_destroy(gn_mpnn* m) {
   if (!m) return;
   cudaSetDevice(m->device);
   if (m->stream) cudaStreamSynchronize(m->stream);
-  void* d[] = {m->d_w, m->d_wb, m->d_g, m->d_m, m->d_v, m->X, m->dq, m->tgt, m->bufA, m->bufB, m->bufC, m->d_loss};
+  void* d[] = {m->d_w, m->d_wb, m->d_g, m->d_m, m->d_v, m->X, m->dq, m->tgt, m->bufA, m->bufB, m->bufC, m->part,
+               m->d_loss};
   for (void* p : d)
     if (p) cudaFree(p);
   for (int l = 0; l < gn::kL; ++l) {
@@ -688,8 +705,9 @@ extern "C" gn_status gn_mpnn_backward(gn_mpnn* m, const gn_graph* g) {
   float* cur = m->bufA;
   float* dz = m->bufB;
   float* spare = m->bufC;
-  k_head_bwd<<<blk(n, 256), 256, 0, s>>>(n, m->Hs[kL - 1], m->d_wb + layer_off(kL), m->dq, cur,
-                                         m->d_g + layer_off(kL));
+  k_head_bwd<<<blk(n, 256), 256, 0, s>>>(n, m->Hs[kL - 1], m->d_wb + layer_off(kL), m->dq, cur, m->part);
+  GN_LAUNCHED();
+  k_reduce_parts<<<blk(kH + 1, 256), 256, 0, s>>>((int)blk(n, 256), kH + 1, m->part, m->d_g + layer_off(kL));
   GN_LAUNCHED();
   const int rows_w = 256;
   for (int l = kL - 1; l >= 0; --l) {
@@ -700,14 +718,18 @@ extern "C" gn_status gn_mpnn_backward(gn_mpnn* m, const gn_graph* g) {
       // the inputs are features: only dZ (for the weights) is needed
       k_dense_bwd_data<kF><<<blk(n, kRows), 256, 0, s>>>(n, cur, m->Zs[l], Wb, dz, spare, spare);
       GN_LAUNCHED();
-      k_dense_bwd_weight<kF><<<blk(n, rows_w), 256, 0, s>>>(n, rows_w, dz, Hin, m->Ms[l], dW);
+      k_dense_bwd_weight<kF><<<blk(n, rows_w), 256, 0, s>>>(n, rows_w, dz, Hin, m->Ms[l], m->part);
+      GN_LAUNCHED();
+      k_reduce_parts<<<blk(2 * kH * kF + kH, 256), 256, 0, s>>>((int)blk(n, rows_w), 2 * kH * kF + kH, m->part, dW);
       GN_LAUNCHED();
     } else {
       // dZ -> dz; dH_in = dZ Ws -> spare; dM_in = dZ Wn -> cur (each CTA reads its rows of cur
       // into shared memory before writing them back)
       k_dense_bwd_data<kH><<<blk(n, kRows), 256, 0, s>>>(n, cur, m->Zs[l], Wb, dz, spare, cur);
       GN_LAUNCHED();
-      k_dense_bwd_weight<kH><<<blk(n, rows_w), 256, 0, s>>>(n, rows_w, dz, Hin, m->Ms[l], dW);
+      k_dense_bwd_weight<kH><<<blk(n, rows_w), 256, 0, s>>>(n, rows_w, dz, Hin, m->Ms[l], m->part);
+      GN_LAUNCHED();
+      k_reduce_parts<<<blk(2 * kH * kH + kH, 256), 256, 0, s>>>((int)blk(n, rows_w), 2 * kH * kH + kH, m->part, dW);
       GN_LAUNCHED();
       // d loss / d H_{l-1} = dH_in + A^T (dM_in / deg)
       k_aggregate_t<kH><<<blk((int64_t)n * 32, 256), 256, 0, s>>>(n, g->d_row_ptr, g->d_col_idx, cur, spare);

@@ -63,6 +63,25 @@ def test_adam_step_matches_reference(env):
     np.testing.assert_allclose(net.params(), want, rtol=1e-5, atol=1e-7)
 
 
+def test_training_is_reproducible(env):
+    """The gradients are summed in a fixed order (per-CTA partials added in CTA order), so two
+    networks from the same seed trained on the same graphs end with the same weights bit for bit
+    and predict the same start."""
+    torch, gn, ws = env
+    train = ws.training_graphs(6, seed=9150, n_lo=3000, n_hi=8000)
+    data = []
+    for inst in train:
+        g = ws.device_graph(inst)
+        t, _ = ws.label(g)
+        data.append((g, t))
+    nets = [ws.WarmStartNet(seed=11) for _ in range(2)]
+    hists = [ws.train(net, data, epochs=3, lr=3e-3) for net in nets]
+    np.testing.assert_array_equal(nets[0].params(), nets[1].params())
+    test = ws.device_graph(inputs.unit_disk_graph(5000, 25000, 9151))
+    np.testing.assert_array_equal(nets[0].predict(test, 0.5).cpu().numpy(), nets[1].predict(test, 0.5).cpu().numpy())
+    assert hists[0][-1] < hists[0][0]
+
+
 def test_training_and_what_the_warm_start_gains(env):
     """Trained on GN's converged states of small unit-disk graphs, the network's start (blended
     with the cold start) reaches a binary state in fewer iterations than the cold start with the
