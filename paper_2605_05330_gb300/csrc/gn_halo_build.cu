@@ -223,55 +223,53 @@ static constexpr int kPadSrc = 0xFFE0;
 // The slots of one send piece: m <= kSendPiece values (owner-local ids, bank = id & 31) in
 // L = round4(m) slots.  The owner's warp stores slots 4j .. 4j + 3 from lane j (one 16-byte
 // store) and gathers their values with four instructions, the u-th reading slot 4j + u of
-// every lane, so the placement decides the bank conflicts of the gathers.  Greedy, values of
-// the busiest banks first: each goes to the instruction u that has a free lane and does not
-// yet read its bank, the least loaded such u first (any u with a free lane when every one
-// reads it).  place[s] = the index of the value in slot s, or -(1 + bank) for padding, bank
-// being one that no value of that instruction reads (where there is one).  Returns L.
+// every lane, so the placement decides the bank conflicts of the gathers.  The rule is a
+// greedy over the values of the busiest banks first (ties by bank, then by value index): each
+// goes to the instruction u that has a free lane and does not yet read its bank, the least
+// loaded such u first, ties to the lowest u (any u with a free lane, least loaded first, when
+// every one reads it).  place[s] = the index of the value in slot s, or -(1 + bank) for
+// padding, bank being one that no value of that instruction reads (where there is one).
+// Returns L.
+//
+// That greedy is a round robin.  A bank's values are placed together, so at a bank's start no
+// instruction reads it yet.  The counts (ordered by count, then u) then always read "the
+// first p instructions hold c + 1 values, the others c", and the least loaded are p, p + 1, ...
+// mod 4.  So the j-th value in bank order goes to instruction j mod 4, whose count is then
+// j / 4 < L / 4: no instruction is full when its turn comes.
 static int place_piece(const int32_t* lid, int m, int* place) {
   const int L = (m + 3) & ~3, lanes = L / 4;
-  // the values bucketed by bank (a counting sort), the banks by decreasing load, ties by bank
-  // (a counting sort of the banks by load)
-  int load[32] = {0};
+  // the banks by decreasing load, ties by bank (a counting sort on maxl - load)
+  int load[32] = {0}, maxl = 0;
   for (int i = 0; i < m; ++i) ++load[lid[i] & 31];
-  int at[32], first[32], bucket[kSendPiece];
-  for (int b = 0, a = 0; b < 32; ++b) {
-    first[b] = at[b] = a;
-    a += load[b];
-  }
-  for (int i = 0; i < m; ++i) bucket[at[lid[i] & 31]++] = i;
-  int nat[kSendPiece + 2] = {0}, border[32];
-  for (int b = 0; b < 32; ++b) ++nat[kSendPiece - load[b] + 1];
-  for (int v = 1; v <= kSendPiece + 1; ++v) nat[v] += nat[v - 1];
-  for (int b = 0; b < 32; ++b) border[nat[kSendPiece - load[b]]++] = b;
-  // each value to the gather u with a free lane that least clashes with its bank, then the least
-  // loaded, then the lowest: the smallest score (capacity, clash, count, u)
-  int cnt[4] = {0, 0, 0, 0}, uof[kSendPiece];
+  for (int b = 0; b < 32; ++b) maxl = std::max(maxl, load[b]);
+  int nat[kSendPiece + 2], border[32];
+  for (int v = 0; v <= maxl + 1; ++v) nat[v] = 0;
+  for (int b = 0; b < 32; ++b) ++nat[maxl - load[b] + 1];
+  for (int v = 1; v <= maxl + 1; ++v) nat[v] += nat[v - 1];
+  for (int b = 0; b < 32; ++b) border[nat[maxl - load[b]]++] = b;
+  // each bank's first rank in that order, and the instructions its ranks a .. a + load - 1 go
+  // to (all four from a load of 4 up): the banks each instruction reads
+  int rank[32];
   uint32_t used[4] = {0, 0, 0, 0};
-  for (int r = 0; r < 32 && load[border[r]] > 0; ++r) {
-    const int bk = border[r];
-    for (int k = first[bk]; k < first[bk] + load[bk]; ++k) {
-      int best = 0, bs = INT_MAX;
-      for (int u = 0; u < 4; ++u) {
-        const int sc = (cnt[u] >= lanes ? (1 << 30) : 0) + (int)((used[u] >> bk & 1u) << 20) + cnt[u] * 4 + u;
-        if (sc < bs) {
-          bs = sc;
-          best = u;
-        }
-      }
-      uof[bucket[k]] = best;
-      ++cnt[best];
-      used[best] |= 1u << bk;
-    }
+  for (int r = 0, a = 0; r < 32; ++r) {
+    const int b = border[r], l = load[b];
+    rank[b] = a;
+    const unsigned x = ((1u << std::min(l, 4)) - 1) << (a & 3), w = (x | x >> 4) & 15u;
+    for (int u = 0; u < 4; ++u) used[u] |= ((w >> u) & 1u) << b;
+    a += l;
   }
-  int pos[4] = {0, 0, 0, 0};
+  // the values in index order: each to instruction (its rank) mod 4, at that instruction's next
+  // lane (four 16-bit lane counters in one word)
+  uint64_t pos = 0;
   for (int i = 0; i < m; ++i) {
-    const int u = uof[i];
-    place[4 * pos[u]++ + u] = i;
+    const int u = rank[lid[i] & 31]++ & 3, sh = 16 * u;
+    place[4 * (int)((pos >> sh) & 0xffff) + u] = i;
+    pos += 1ull << sh;
   }
-  for (int u = 0; u < 4; ++u) {
+  // instructions m mod 4 .. 3 hold one value fewer: their last lane is padding
+  for (int u = m & 3; u != 0 && u < 4; ++u) {
     const int zb = used[u] == 0xffffffffu ? 0 : __builtin_ctz(~used[u]);
-    for (int j = pos[u]; j < lanes; ++j) place[4 * j + u] = -1 - zb;
+    place[4 * (lanes - 1) + u] = -1 - zb;
   }
   return L;
 }

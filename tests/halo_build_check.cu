@@ -1,7 +1,8 @@
 // Host-side checks of the halo block builder's slice colouring and send-piece placement
 // (gn_halo_build.cu, included here for its file-local functions), linked against libgn.so for
-// the rest.  No GPU is used.  Prints "ok" and returns 0 when every check passes; prints what
+// the rest.  The placement is compared slot for slot with its rule written out plainly.  No GPU is used.  Prints "ok" and returns 0 when every check passes; prints what
 // failed and returns 1 otherwise.
+#include <algorithm>
 #include <cstdio>
 #include <random>
 #include <vector>
@@ -68,15 +69,67 @@ static void check_colouring(std::mt19937& rng) {
   }
 }
 
+// The send-piece rule written out as stated: values of the busiest banks first (ties by bank,
+// then by index), each to the instruction with a free lane that does not yet read its bank, the
+// least loaded such first, ties to the lowest; when every instruction with a free lane reads it,
+// the least loaded of those.  Lanes of an instruction in value order; padding names the lowest
+// bank the instruction does not read.
+static int greedy_placement(const int32_t* lid, int m, int* place) {
+  const int L = (m + 3) & ~3, lanes = L / 4;
+  std::vector<int> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i;
+  int load[32] = {0};
+  for (int i = 0; i < m; ++i) ++load[lid[i] & 31];
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ba = lid[a] & 31, bb = lid[b] & 31;
+    if (load[ba] != load[bb]) return load[ba] > load[bb];
+    if (ba != bb) return ba < bb;
+    return a < b;
+  });
+  std::vector<int> uof(m);
+  int cnt[4] = {0, 0, 0, 0};
+  uint32_t reads[4] = {0, 0, 0, 0};
+  for (int i : order) {
+    const int bk = lid[i] & 31;
+    int best = -1;
+    for (int pass = 0; pass < 2 && best < 0; ++pass)
+      for (int u = 0; u < 4; ++u) {
+        if (cnt[u] >= lanes || (pass == 0 && (reads[u] >> bk & 1u))) continue;
+        if (best < 0 || cnt[u] < cnt[best]) best = u;
+      }
+    uof[i] = best;
+    ++cnt[best];
+    reads[best] |= 1u << bk;
+  }
+  int next[4] = {0, 0, 0, 0};
+  for (int i = 0; i < m; ++i) place[4 * next[uof[i]]++ + uof[i]] = i;
+  for (int u = 0; u < 4; ++u) {
+    int zb = 0;
+    while (zb < 32 && (reads[u] >> zb & 1u)) ++zb;
+    if (zb == 32) zb = 0;
+    for (int j = next[u]; j < lanes; ++j) place[4 * j + u] = -1 - zb;
+  }
+  return L;
+}
+
 static void check_placement(std::mt19937& rng) {
   int32_t lid[gn::kSendPiece];
   int place[gn::kSendPiece];
   for (int t = 0; t < 100000; ++t) {
     const int m = 1 + (int)(rng() % gn::kSendPiece);
     const int span = 32 + (int)(rng() % 5000);
-    for (int i = 0; i < m; ++i) lid[i] = (int32_t)(rng() % (unsigned)span);
+    const unsigned crowd = t % 3 == 0 ? 1 + rng() % 4 : 0;  // a few banks take many of the values
+    for (int i = 0; i < m; ++i) {
+      lid[i] = (int32_t)(rng() % (unsigned)span);
+      if (crowd && rng() % 2) lid[i] = (lid[i] & ~31) | (int32_t)(rng() % crowd);
+    }
     const int L = gn::place_piece(lid, m, place);
     CHECK(L == ((m + 3) & ~3), "a piece takes m rounded up to 4 slots");
+    int want[gn::kSendPiece];
+    greedy_placement(lid, m, want);
+    bool same = true;
+    for (int q = 0; q < L; ++q) same = same && place[q] == want[q];
+    CHECK(same, "the placement is the stated greedy's, slot for slot");
     std::vector<int> seen(m, 0);
     bool ok = true;
     uint32_t banks[4] = {0, 0, 0, 0};
