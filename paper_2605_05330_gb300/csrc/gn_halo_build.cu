@@ -207,14 +207,32 @@ static void color_slice64(int W, const uint16_t (*lid)[64], const int* nl, uint8
 // then the pull exchange reads few sectors and wins; below it the push exchange does.
 static constexpr double kPullDensity = 4.0;
 
-// Builds the blocks for the partition `part`, for the exchange `want` (GN_GATHER_HALO: by
-// the halo density; GN_GATHER_HALO_PULL / _PUSH: that one).  Sets *fits = false (and builds
-// nothing on the device) when a CTA's working set does not fit shared memory or 16-bit local
-// ids; with the automatic choice the other exchange is tried before giving up.  The per-CTA
-// work runs on the host threads, a CTA at a time (parallel_items); every CTA's output is its own.
-static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
-                                   const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
-                                   bool push, size_t smem_limit, bool* fits);
+// The halo mode's host side, in three steps:
+//  - halo_lists: each CTA's distinct external neighbours (its halo), in increasing id order,
+//    with the 32-byte sectors of the state vector they touch (the exchange is chosen by their
+//    density);
+//  - encode_halo_blocks: the packed per-CTA blocks for one exchange, in host memory;
+//  - build_halo: both, for the exchange `want` (GN_GATHER_HALO: by the halo density;
+//    GN_GATHER_HALO_PULL / _PUSH: that one), and the upload.  *fits = false (and nothing is
+//    built on the device) when a CTA's working set does not fit shared memory or 16-bit local
+//    ids; with the automatic choice the other exchange is tried before giving up.
+// The per-CTA work runs on the host threads, a CTA at a time (parallel_items); every CTA's
+// output is its own.
+struct HaloBlocks {
+  bool fits = false;
+  int R = 0;                  // rows per CTA, padded to 4 (local ids of the halo start here)
+  int Lp = 0;                 // the longest halo, padded to 4 (32 zero slots follow it)
+  size_t smem = 0;            // dynamic shared memory of the kernel
+  int64_t inbox_slots = 0;    // push: all CTAs' inbox slots
+  std::vector<int64_t> hoff;  // [nblocks + 1] byte offsets of the blocks in blob
+  std::unique_ptr<unsigned char[]> blob;
+  size_t blob_bytes = 0;
+};
+static void halo_lists(int n, const std::vector<int32_t>& rp, const int32_t* ci, const std::vector<int32_t>& part,
+                       std::vector<std::vector<int32_t>>& ext, int64_t* vals, int64_t* sectors);
+static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int32_t* ci,
+                               const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                               bool push, size_t smem_limit, HaloBlocks* out);
 
 // Padding in a send list: the id field holds kPadSrc | bank, read as the zero slot of that bank
 // once the blocks' zero slots are placed (owner-local ids are below 32768).
@@ -279,11 +297,44 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   *fits = false;
   const int nb = (int)part.size() - 1;
   const int n = g->n;
-
-  // halos: each CTA's distinct external neighbours in increasing id order, from a bitmap of
-  // the vertex range (a mark per entry, then a scan of the marked words), and the number of
-  // 32-byte sectors of the state vector they touch
   std::vector<std::vector<int32_t>> ext(nb);
+  int64_t vals = 0, sectors = 0;
+  halo_lists(n, rp, ci, part, ext, &vals, &sectors);
+  // the exchange: forced, or by the density of the halos in memory
+  bool push = want == GN_GATHER_HALO_PUSH ||
+              (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
+  HaloBlocks hb;
+  for (int attempt = 0; attempt < 2 && !hb.fits; ++attempt, push = !push) {
+    if (attempt == 1 && want != GN_GATHER_HALO) break;
+    encode_halo_blocks(n, rp, ci, part, ext, push, smem_limit, &hb);
+    if (hb.fits) break;
+  }
+  if (!hb.fits) return GN_OK;
+  GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
+  GN_CUDA(cudaMalloc(&g->d_hblob, hb.blob_bytes));
+  // the exchange buffers: push, the inboxes; pull, one slot per vertex (read by the tagged
+  // exchange only); three of each (two alternate under the barrier or the flags, three rotate
+  // in the tagged exchange)
+  g->inbox_len = push ? std::max<int64_t>(hb.inbox_slots, 4) : (int64_t)((n + 3) & ~3);
+  GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 3 * (size_t)g->inbox_len));
+  GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 3 * (size_t)g->inbox_len, g->stream));
+  g->halo_push = push;
+  GN_CUDA(cudaMemcpyAsync(g->d_hoff, hb.hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                          g->stream));
+  GN_CUDA(cudaMemcpyAsync(g->d_hblob, hb.blob.get(), hb.blob_bytes, cudaMemcpyHostToDevice, g->stream));
+  GN_CUDA(cudaStreamSynchronize(g->stream));
+  g->halo_pad = hb.Lp;
+  g->rows_pad_halo = hb.R;
+  g->smem_bytes = hb.smem;
+  *fits = true;
+  return GN_OK;
+}
+
+// The halo lists, from a bitmap of the vertex range per host thread (a mark per entry, then a
+// scan of the marked words).
+static void halo_lists(int n, const std::vector<int32_t>& rp, const int32_t* ci, const std::vector<int32_t>& part,
+                       std::vector<std::vector<int32_t>>& ext, int64_t* vals, int64_t* sectors) {
+  const int nb = (int)part.size() - 1;
   std::vector<int64_t> sectors_of(nb, 0);
   std::vector<std::vector<uint64_t>> bitmaps(host_threads());  // per host thread, kept all-zero
   parallel_items(nb, [&](int b, int t) {
@@ -319,29 +370,20 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
       sectors_of[b] = sec;
     }
   });
-  int64_t vals = 0, sectors = 0;
+  *vals = 0;
+  *sectors = 0;
   for (int b = 0; b < nb; ++b) {
-    vals += (int64_t)ext[b].size();
-    sectors += sectors_of[b];
+    *vals += (int64_t)ext[b].size();
+    *sectors += sectors_of[b];
   }
-  // the exchange: forced, or by the density of the halos in memory
-  bool push = want == GN_GATHER_HALO_PUSH ||
-              (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
-  for (int attempt = 0; attempt < 2; ++attempt, push = !push) {
-    if (attempt == 1 && want != GN_GATHER_HALO) break;
-    gn_status st = build_halo_blocks(g, rp, ci, part, ext, push, smem_limit, fits);
-    if (st != GN_OK || *fits) return st;
-  }
-  return GN_OK;
 }
 
 // The blocks for one exchange (see build_halo).
-static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, const int32_t* ci,
-                                   const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
-                                   bool push, size_t smem_limit, bool* fits) {
-  *fits = false;
+static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int32_t* ci,
+                               const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
+                               bool push, size_t smem_limit, HaloBlocks* out) {
+  out->fits = false;
   const int nb = (int)part.size() - 1;
-  const int n = g->n;
   int max_rows = 0;
   for (int b = 0; b < nb; ++b) max_rows = std::max(max_rows, part[b + 1] - part[b]);
   const int R = (max_rows + 3) & ~3;
@@ -380,7 +422,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       lxp[c] = total;
     });
     for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + lxp[c];
-    if (inbox_off[nb] > (int64_t)INT32_MAX) return GN_OK;  // inbox slots do not fit 32 bits
+    if (inbox_off[nb] > (int64_t)INT32_MAX) return;  // inbox slots do not fit 32 bits
     // where each run goes in its owner's lists: consumers in order
     std::vector<std::vector<int2>> roff(nb);  // per consumer and run: (first source, first piece)
     std::vector<int64_t> scount(nb, 0), pcount(nb, 0);
@@ -581,7 +623,7 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
   const int zero_id = R + Lp;  // 32 zero slots from here, one per bank
   const size_t floats = (size_t)6 * R + Lp + 32;
   const size_t smem = 4 * floats + blk_max;
-  if (zero_id + 31 > 65535 || smem > smem_limit || R > 32767) return GN_OK;  // does not fit
+  if (zero_id + 31 > 65535 || smem > smem_limit || R > 32767) return;  // does not fit
   std::vector<int64_t> hoff(nb + 1, 0);
   for (int b = 0; b < nb; ++b) hoff[b + 1] = hoff[b] + plans[b].H.bytes;
   const size_t blob_bytes = (size_t)std::max<int64_t>(hoff[nb], 16);
@@ -794,23 +836,14 @@ static gn_status build_halo_blocks(gn_graph* g, const std::vector<int32_t>& rp, 
       }
     }
   });
-  GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
-  GN_CUDA(cudaMalloc(&g->d_hblob, blob_bytes));
-  // the exchange buffers: push, the inboxes; pull, one slot per vertex (read by the tagged
-  // exchange only); three of each (two alternate under the barrier or the flags, three rotate
-  // in the tagged exchange)
-  g->inbox_len = push ? std::max<int64_t>(inbox_off[nb], 4) : (int64_t)((n + 3) & ~3);
-  GN_CUDA(cudaMalloc(&g->d_inbox, sizeof(float) * 3 * (size_t)g->inbox_len));
-  GN_CUDA(cudaMemsetAsync(g->d_inbox, 0, sizeof(float) * 3 * (size_t)g->inbox_len, g->stream));
-  g->halo_push = push;
-  GN_CUDA(cudaMemcpyAsync(g->d_hoff, hoff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, g->stream));
-  GN_CUDA(cudaMemcpyAsync(g->d_hblob, blob.get(), blob_bytes, cudaMemcpyHostToDevice, g->stream));
-  GN_CUDA(cudaStreamSynchronize(g->stream));
-  g->halo_pad = Lp;
-  g->rows_pad_halo = R;
-  g->smem_bytes = smem;
-  *fits = true;
-  return GN_OK;
+  out->R = R;
+  out->Lp = Lp;
+  out->smem = smem;
+  out->inbox_slots = push ? inbox_off[nb] : 0;
+  out->hoff = std::move(hoff);
+  out->blob = std::move(blob);
+  out->blob_bytes = blob_bytes;
+  out->fits = true;
 }
 
 }  // namespace gn

@@ -1,6 +1,7 @@
-// Host-side checks of the halo block builder's slice colouring and send-piece placement
-// (gn_halo_build.cu, included here for its file-local functions), linked against libgn.so for
-// the rest.  The placement is compared slot for slot with its rule written out plainly.  No GPU is used.  Prints "ok" and returns 0 when every check passes; prints what
+// Host-side checks of the halo block builder (gn_halo_build.cu, included here for its
+// file-local functions), linked against libgn.so for the rest: the slice colouring, the
+// send-piece placement (slot for slot against its rule written out plainly), the halo lists,
+// and the decoded blocks of both exchanges on random graphs.  No GPU is used.  Prints "ok" and returns 0 when every check passes; prints what
 // failed and returns 1 otherwise.
 #include <algorithm>
 #include <cstdio>
@@ -153,10 +154,195 @@ static void check_placement(std::mt19937& rng) {
   }
 }
 
+// A random simple graph: each vertex i draws neighbours within a window around i (locality, so
+// interior rows and dense halos occur) or anywhere (cut edges), a few hubs draw hundreds
+// (heavy rows); symmetrised, deduplicated and sorted.
+static void random_graph(std::mt19937& rng, int n, int deg, int window, int hubs, std::vector<int32_t>& rp,
+                         std::vector<int32_t>& ci) {
+  std::vector<std::vector<int32_t>> adj(n);
+  for (int i = 0; i < n; ++i) {
+    const int d = i < hubs ? 150 + (int)(rng() % 300) : (int)(rng() % (2 * deg + 1));
+    for (int t = 0; t < d; ++t) {
+      int j = (window > 0 && rng() % 4 != 0) ? i - window + (int)(rng() % (2 * window + 1)) : (int)(rng() % n);
+      if (j < 0 || j >= n || j == i) continue;
+      adj[i].push_back(j);
+      adj[j].push_back(i);
+    }
+  }
+  rp.assign(n + 1, 0);
+  ci.clear();
+  for (int i = 0; i < n; ++i) {
+    std::sort(adj[i].begin(), adj[i].end());
+    adj[i].erase(std::unique(adj[i].begin(), adj[i].end()), adj[i].end());
+    ci.insert(ci.end(), adj[i].begin(), adj[i].end());
+    rp[i + 1] = (int32_t)ci.size();
+  }
+}
+
+// Decodes every CTA's block and checks what the kernel relies on: each row is summed once (a
+// SELL lane or a heavy row), its real ids name exactly its neighbours (own rows, halo slots whose
+// value is the right vertex's, through the pull list or the owners' send lists), everything else
+// reads a zero slot, padding in a SELL column reads a bank no real entry of that column reads,
+// interior slices read no halo, the dependency list names the halo's owners, and in push mode
+// the owners' send pieces fill every inbox slot once.
+static void check_blocks(const char* name, int n, const std::vector<int32_t>& rp, const std::vector<int32_t>& ci,
+                         int nb, bool push) {
+  std::vector<int32_t> part(nb + 1);
+  for (int b = 0; b <= nb; ++b) part[b] = (int32_t)((int64_t)n * b / nb);
+  std::vector<std::vector<int32_t>> ext(nb);
+  int64_t vals = 0, sectors = 0;
+  gn::halo_lists(n, rp, ci.data(), part, ext, &vals, &sectors);
+  // the halo lists against their definition
+  bool lists_ok = true;
+  int64_t want_vals = 0, want_sectors = 0;
+  for (int b = 0; b < nb; ++b) {
+    std::vector<int32_t> x;
+    for (int64_t e = rp[part[b]]; e < rp[part[b + 1]]; ++e)
+      if (ci[e] < part[b] || ci[e] >= part[b + 1]) x.push_back(ci[e]);
+    std::sort(x.begin(), x.end());
+    x.erase(std::unique(x.begin(), x.end()), x.end());
+    lists_ok = lists_ok && x == ext[b];
+    want_vals += (int64_t)x.size();
+    for (size_t t = 0; t < x.size(); ++t) want_sectors += (t == 0 || (x[t] >> 3) != (x[t - 1] >> 3));
+  }
+  CHECK(lists_ok && vals == want_vals && sectors == want_sectors, name);
+  gn::HaloBlocks hb;
+  gn::encode_halo_blocks(n, rp, ci.data(), part, ext, push, 220 * 1024, &hb);
+  CHECK(hb.fits, name);
+  if (!hb.fits) return;
+  const int R = hb.R, zero_id = R + hb.Lp;
+  auto header = [&](int b) { return reinterpret_cast<const gn::HaloHeader*>(hb.blob.get() + hb.hoff[b]); };
+  auto at = [&](int b, int off) { return hb.blob.get() + hb.hoff[b] + off; };
+  // push: the vertex each inbox slot receives, from the owners' send lists
+  std::vector<int32_t> inbox;
+  bool pieces_ok = true;
+  if (push) {
+    inbox.assign((size_t)hb.inbox_slots, -2);  // -2: unwritten, -1: padding
+    for (int o = 0; o < nb; ++o) {
+      const gn::HaloHeader* H = header(o);
+      const int4* pc = reinterpret_cast<const int4*>(at(o, H->off_piece));
+      const uint16_t* src = reinterpret_cast<const uint16_t*>(at(o, H->off_src));
+      for (int p = 0; p < H->npiece; ++p) {
+        const int4 q = pc[p];
+        pieces_ok = pieces_ok && q.x % 4 == 0 && q.y % 4 == 0 && q.z % 4 == 0 && q.y > 0 && q.y <= gn::kSendPiece &&
+                    q.x + q.y <= hb.inbox_slots;
+        if (!pieces_ok) break;
+        for (int k = 0; k < q.y; ++k) {
+          const int sv = src[q.z + k];
+          const bool pad = sv >= zero_id && sv < zero_id + 32;
+          pieces_ok = pieces_ok && inbox[q.x + k] == -2 && (pad || sv < part[o + 1] - part[o]);
+          inbox[q.x + k] = pad ? -1 : part[o] + sv;
+        }
+      }
+    }
+    for (int32_t v : inbox) pieces_ok = pieces_ok && v != -2;
+    CHECK(pieces_ok, name);
+    if (!pieces_ok) return;
+  }
+  bool rows_ok = true, ids_ok = true, pad_ok = true, interior_ok = true, dep_ok = true, halo_ok = true;
+  for (int b = 0; b < nb; ++b) {
+    const gn::HaloHeader* H = header(b);
+    const int rb = part[b], nr = part[b + 1] - rb;
+    // the vertex a local id reads: own row, halo value, or -1 for a zero slot (-3: invalid)
+    std::vector<int32_t> halo(H->lx, -1);
+    if (push) {
+      for (int h = 0; h < H->lx; ++h) halo[h] = inbox[H->inbox_off + h];
+    } else {
+      const int32_t* x = reinterpret_cast<const int32_t*>(at(b, H->off_x));
+      for (int h = 0; h < H->lx; ++h) halo[h] = x[h];
+    }
+    auto vertex = [&](int id) -> int32_t {
+      if (id < nr) return rb + id;
+      if (id >= R && id < R + H->lx) return halo[id - R];
+      if (id >= zero_id && id < zero_id + 32) return -1;
+      return -3;
+    };
+    // the halo holds exactly the CTA's external neighbours; its owners are the dependency list
+    std::vector<int32_t> hv;
+    for (int32_t v : halo)
+      if (v >= 0) hv.push_back(v);
+    std::sort(hv.begin(), hv.end());
+    halo_ok = halo_ok && hv == ext[b];
+    std::vector<int32_t> owners;
+    for (int32_t v : hv) {
+      const int o = (int)(std::upper_bound(part.begin(), part.end(), v) - part.begin()) - 1;
+      if (owners.empty() || owners.back() != o) owners.push_back(o);
+    }
+    const int32_t* dep = reinterpret_cast<const int32_t*>(at(b, H->off_dep));
+    dep_ok = dep_ok && H->ndep == (int)owners.size() && std::equal(owners.begin(), owners.end(), dep);
+    std::vector<int> seen(nr, 0);
+    std::vector<std::vector<int32_t>> got(nr);
+    const int2* meta = reinterpret_cast<const int2*>(at(b, H->off_meta));
+    const short* srow = reinterpret_cast<const short*>(at(b, H->off_srow));
+    const uint16_t* sell = reinterpret_cast<const uint16_t*>(at(b, H->off_sell));
+    for (int sl = 0; sl < H->ns; ++sl) {
+      const int base = meta[sl].x, W = meta[sl].y;
+      for (int k = 0; k < W; ++k) {
+        uint32_t real_banks = 0, pad_banks = 0;
+        for (int l = 0; l < 32; ++l) {
+          const int id = sell[base + (k >> 2) * 128 + l * 4 + (k & 3)], r = srow[sl * 32 + l];
+          const int32_t v = vertex(id);
+          ids_ok = ids_ok && v != -3 && (r >= 0 || v == -1);
+          if (v >= 0 && r >= 0) {
+            got[r].push_back(v);
+            real_banks |= 1u << (id & 31);
+            interior_ok = interior_ok && (sl >= H->ns_int || id < nr);
+          } else {
+            pad_banks |= 1u << (id & 31);
+          }
+        }
+        pad_ok = pad_ok && (real_banks == 0xffffffffu || !(pad_banks & real_banks));
+      }
+      for (int l = 0; l < 32; ++l)
+        if (srow[sl * 32 + l] >= 0) ++seen[srow[sl * 32 + l]];
+    }
+    const int* hm = reinterpret_cast<const int*>(at(b, H->off_hmeta));
+    const int* hc = reinterpret_cast<const int*>(at(b, H->off_hchunk));
+    const uint16_t* hl = reinterpret_cast<const uint16_t*>(at(b, H->off_hl));
+    for (int h = 0; h < H->nheavy; ++h) {
+      const int r = hm[3 * h];
+      ++seen[r];
+      for (int c = hm[3 * h + 1]; c < hm[3 * h + 1] + hm[3 * h + 2]; ++c)
+        for (int k = 0; k < hc[2 * c + 1]; ++k) {
+          const int32_t v = vertex(hl[hc[2 * c] + k]);
+          ids_ok = ids_ok && v >= 0;
+          got[r].push_back(v);
+        }
+    }
+    for (int r = 0; r < nr; ++r) {
+      rows_ok = rows_ok && seen[r] == 1;
+      std::sort(got[r].begin(), got[r].end());
+      ids_ok = ids_ok && std::equal(got[r].begin(), got[r].end(), ci.begin() + rp[rb + r],
+                                    ci.begin() + rp[rb + r + 1]) &&
+               (int64_t)got[r].size() == rp[rb + r + 1] - rp[rb + r];
+    }
+  }
+  CHECK(rows_ok, name);
+  CHECK(ids_ok, name);
+  CHECK(pad_ok, name);
+  CHECK(interior_ok, name);
+  CHECK(dep_ok, name);
+  CHECK(halo_ok, name);
+}
+
+static void check_all_blocks(std::mt19937& rng) {
+  std::vector<int32_t> rp, ci;
+  random_graph(rng, 9000, 6, 40, 4, rp, ci);  // local, with hubs: interior slices, dense halos
+  check_blocks("blocks, local graph, pull", 9000, rp, ci, 11, false);
+  check_blocks("blocks, local graph, push", 9000, rp, ci, 11, true);
+  random_graph(rng, 6000, 8, 0, 3, rp, ci);  // random: most edges cut
+  check_blocks("blocks, random graph, pull", 6000, rp, ci, 7, false);
+  check_blocks("blocks, random graph, push", 6000, rp, ci, 7, true);
+  random_graph(rng, 300, 3, 5, 0, rp, ci);  // one slice per CTA, ragged
+  check_blocks("blocks, small graph, push", 300, rp, ci, 3, true);
+  check_blocks("blocks, small graph, pull", 300, rp, ci, 3, false);
+}
+
 int main() {
   std::mt19937 rng(20261204);
   check_colouring(rng);
   check_placement(rng);
+  check_all_blocks(rng);
   if (failures) {
     std::printf("%d failures\n", failures);
     return 1;
