@@ -1,9 +1,13 @@
-"""The halo block builder's host steps on random inputs: the 64-colour slice colouring gives the
-same columns as the general one and both are proper edge colourings of the lanes x banks
-multigraph (every lane's entries in distinct columns, every column's entries in distinct banks,
-no column at or past the width), and each send piece's placement puts every value in exactly one
-slot, with padding that reads a bank its gather leaves free.  Host code only: a small program
-that includes the builder's source (tests/halo_build_check.cu)."""
+"""The halo block builder's host steps on random inputs:
+- the 64-colour slice colouring gives the same columns as the general one, and both are proper
+  edge colourings of the lanes x banks multigraph (every lane's entries in distinct columns,
+  every column's entries in distinct banks, no column at or past the width);
+- each send piece's placement equals its greedy rule written out, slot for slot, with every
+  value in exactly one slot and padding on a bank its gather leaves free;
+- the halo lists match their definition, and every CTA's decoded block, in both exchanges,
+  sums each row once over exactly its neighbours' values (own rows, pull lists, the owners'
+  send lists), with zero slots everywhere else.
+Host code only: a small program that includes the builder's source (tests/halo_build_check.cu)."""
 import os
 import subprocess
 
