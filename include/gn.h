@@ -127,7 +127,7 @@ void gn_default_params(gn_params* p);
  * gn_create -- a1 of the path: validate, upload and prepare a graph.  Sec. 2: A must be
  * the adjacency matrix of a simple undirected graph (symmetric, zero diagonal); Def. WRGN:
  * w in R_{++}^n, v = sqrt(w).
- *   n        number of vertices, 0 <= n < 2^31
+ *   n        number of vertices, 0 <= n < 2^31 - 1
  *   row_ptr  int32[n+1], row_ptr[0] = 0, non-decreasing; nnz = row_ptr[n] directed entries
  *   col_idx  int32[nnz]; row i lists N(i) strictly increasing, no i itself; j in N(i)
  *            iff i in N(j)
@@ -146,8 +146,10 @@ gn_status gn_create(gn_graph** g, int32_t n, const int32_t* row_ptr, const int32
 #define GN_GATHER_SMEM_CSR 2  /* each CTA's neighbour ids in shared memory, values through L1/L2 */
 #define GN_GATHER_HALO 3      /* each CTA's distinct external neighbours staged in shared memory,
                                  exchanged by pull or push as the halo density suggests */
-#define GN_GATHER_HALO_PULL 4 /* halo mode, pull exchange (per-value gathers from the state vector) */
-#define GN_GATHER_HALO_PUSH 5 /* halo mode, push exchange (per-CTA inboxes fetched by bulk copy) */
+#define GN_GATHER_HALO_PULL 4 /* halo mode, pull exchange (each halo value read from its owner's
+                                 slot) */
+#define GN_GATHER_HALO_PUSH 5 /* halo mode, push exchange (owners write per-consumer inboxes that
+                                 the consumer reads) */
 
 typedef struct {
   int reorder;          /* GN_REORDER_* */

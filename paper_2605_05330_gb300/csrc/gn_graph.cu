@@ -394,9 +394,9 @@ extern "C" gn_status gn_create_ex(gn_graph** out, int32_t n, const int32_t* row_
   const int reorder = opts ? opts->reorder : GN_REORDER_NONE;
   const int gather = opts ? opts->gather : GN_GATHER_AUTO;
   if (!out) return fail(GN_ERR_ARG, "gn_create: out is NULL");
-  if (gather < GN_GATHER_AUTO || gather > GN_GATHER_HALO_PUSH) return fail(GN_ERR_ARG, "gn_create: bad gather mode");
   *out = nullptr;
-  if (n < 0 || !row_ptr || (!w && n > 0) || (mem != GN_HOST && mem != GN_DEVICE) ||
+  if (gather < GN_GATHER_AUTO || gather > GN_GATHER_HALO_PUSH) return fail(GN_ERR_ARG, "gn_create: bad gather mode");
+  if (n < 0 || n == INT32_MAX || !row_ptr || (!w && n > 0) || (mem != GN_HOST && mem != GN_DEVICE) ||
       reorder < GN_REORDER_NONE || reorder > GN_REORDER_DEGREE)
     return fail(GN_ERR_ARG, "gn_create: bad argument");
 

@@ -577,8 +577,9 @@ extern "C" void gn_mpnn_destroy(gn_mpnn* m) {
 
 extern "C" gn_status gn_mpnn_create(gn_mpnn** out, const float* init_params_host, void* stream) {
   using namespace gn;
-  if (!out || !init_params_host) return fail(GN_ERR_ARG, "gn_mpnn_create: bad argument");
+  if (!out) return fail(GN_ERR_ARG, "gn_mpnn_create: out is NULL");
   *out = nullptr;
+  if (!init_params_host) return fail(GN_ERR_ARG, "gn_mpnn_create: init_params is NULL");
   gn_mpnn* m = new gn_mpnn();
   struct Guard {
     gn_mpnn*& m;
