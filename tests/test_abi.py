@@ -100,6 +100,45 @@ def test_create_rejects_bad_arguments_on_the_host(libgn):
     assert libgn.gn_mpnn_create(ctypes.byref(h), None, None) == GN_ERR_ARG and not h.value
 
 
+def test_null_handles_are_rejected_on_the_host(libgn):
+    """Every entry point that takes a handle answers a NULL one with GN_ERR_ARG (the queries with
+    0, the destructors with nothing) before any device call, so this runs without a GPU."""
+    L, d, f = libgn, ctypes.c_double, ctypes.c_float
+    for destroy in (L.gn_destroy, L.gn_batch_destroy, L.gn_mpnn_destroy):
+        destroy(None)
+    for query in (L.gn_gather_mode, L.gn_halo_exchange, L.gn_num_vertices, L.gn_vertex_order_source):
+        assert query(None) == 0
+    L.gn_num_entries.restype = ctypes.c_int64
+    assert L.gn_num_entries(None) == 0
+    calls = {
+        "gn_set_io": lambda: L.gn_set_io(None, 0),
+        "gn_set_weights": lambda: L.gn_set_weights(None, None),
+        "gn_vertex_order": lambda: L.gn_vertex_order(None, None),
+        "gn_run": lambda: L.gn_run(None, None, 10, d(1e-7), None, 0, None, None),
+        "gn_extract_is": lambda: L.gn_extract_is(None, None, None, None, None, None),
+        "gn_objective": lambda: L.gn_objective(None, None, d(1.5), None, None),
+        "gn_backward": lambda: L.gn_backward(None, None, None, None),
+        "gn_run_noalloc": lambda: L.gn_run_noalloc(-1, None, None, None, None, 10, d(1e-7), None, 0, None, None,
+                                                   None),
+        "gn_batch_run": lambda: L.gn_batch_run(None, None, 10, d(1e-7), None, None, None),
+        "gn_batch_set_threads": lambda: L.gn_batch_set_threads(None, 256),
+        "gn_batch_set_packing": lambda: L.gn_batch_set_packing(None, 64),
+        "gn_batch_packing": lambda: L.gn_batch_packing(None, None, None),
+        "gn_batch_tune": lambda: L.gn_batch_tune(None, None, 10, None),
+        "gn_batch_extract": lambda: L.gn_batch_extract(None, None, None, None, None),
+        "gn_random_start": lambda: L.gn_random_start(ctypes.c_int64(-1), None, None, None),
+        "gn_mpnn_forward": lambda: L.gn_mpnn_forward(None, None, None, None, None),
+        "gn_mpnn_predict": lambda: L.gn_mpnn_predict(None, None, f(0.5), None),
+        "gn_mpnn_backward": lambda: L.gn_mpnn_backward(None, None),
+        "gn_mpnn_zero_grad": lambda: L.gn_mpnn_zero_grad(None),
+        "gn_mpnn_step": lambda: L.gn_mpnn_step(None, f(1e-3)),
+        "gn_mpnn_get_params": lambda: L.gn_mpnn_get_params(None, None),
+        "gn_mpnn_get_grads": lambda: L.gn_mpnn_get_grads(None, None),
+    }
+    wrong = {name: st for name, st in ((name, call()) for name, call in calls.items()) if st != -1}
+    assert not wrong, wrong
+
+
 def test_oracle_is_not_imported_by_the_product():
     """The product path (package, bench CUDA leg) never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_2605_05330_gb300")
