@@ -681,15 +681,16 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
       }
       HaloHeader* H = reinterpret_cast<HaloHeader*>(B);
       H->zero_id = zero_id;
+      // a vertex's local id is R + extpos[j]: halo slots from R up, own rows below (no branch
+      // per entry)
       for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = push ? hslot[b][t] : (int32_t)t;
+      for (int j = rb; j < re; ++j) extpos[j] = j - rb - R;
       if (push) {  // the padding of the send list reads the zero slot of the bank it names
         uint16_t* sp = reinterpret_cast<uint16_t*>(B + H->off_src);
         for (size_t e = 0; e < plans[b].src.size(); ++e)
           if (sp[e] >= kPadSrc) sp[e] = (uint16_t)(zero_id + (((sp[e] & 31) - zero_id) & 31));
       }
-      auto lid = [&](int j) -> uint16_t {
-        return (uint16_t)((j >= rb && j < re) ? (j - rb) : (R + extpos[j]));
-      };
+      auto lid = [&](int j) -> uint16_t { return (uint16_t)(R + extpos[j]); };
       const int2* meta = reinterpret_cast<const int2*>(B + H->off_meta);
       const short* srow = reinterpret_cast<const short*>(B + H->off_srow);
       uint16_t* sell = reinterpret_cast<uint16_t*>(B + H->off_sell);
