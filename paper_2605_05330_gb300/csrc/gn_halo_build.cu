@@ -234,10 +234,6 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
                                const std::vector<int32_t>& part, const std::vector<std::vector<int32_t>>& ext,
                                bool push, size_t smem_limit, HaloBlocks* out);
 
-// Padding in a send list: the id field holds kPadSrc | bank, read as the zero slot of that bank
-// once the blocks' zero slots are placed (owner-local ids are below 32768).
-static constexpr int kPadSrc = 0xFFE0;
-
 // The slots of one send piece: m <= kSendPiece values (owner-local ids, bank = id & 31) in
 // L = round4(m) slots.  The owner's warp stores slots 4j .. 4j + 3 from lane j (one 16-byte
 // store) and gathers their values with four instructions, the u-th reading slot 4j + u of
@@ -393,7 +389,8 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
   // multiple of 4 slots and is padded to one, and its pieces of kSendPiece slots are placed by
   // place_piece.  The owner o sends its runs consumer by consumer: a piece (first inbox slot,
   // length, first source, 0) per kSendPiece slots from each run's start, and the source id of
-  // every slot (the owner-local id read, or for padding kPadSrc | bank).  hslot: the inbox slot
+  // every slot (the owner-local id read, or for padding the zero slot of the bank place_piece
+  // names).  hslot: the inbox slot
   // (within c's region) of ext[c][t].  Pull: the halo in ext order, 4-slot aligned regions.
   struct Sends {
     std::vector<int4> pieces;  // all four fields multiples of 4 (but the last)
@@ -402,9 +399,9 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
   std::vector<Sends> sends(nb);
   std::vector<std::vector<int32_t>> hslot(nb);
   std::vector<int64_t> lxp(nb), inbox_off(nb + 1, 0);
+  std::vector<std::vector<int2>> hrun(push ? nb : 0);  // push: each consumer's runs
   if (push) {
     // each consumer's runs, (owner, padded length) in owner order
-    std::vector<std::vector<int2>> hrun(nb);
     parallel_items(nb, [&](int c, int) {
       const std::vector<int32_t>& xc = ext[c];
       std::vector<int2>& runs = hrun[c];
@@ -421,6 +418,17 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
       }
       lxp[c] = total;
     });
+  } else {
+    for (int c = 0; c < nb; ++c) lxp[c] = (int64_t)ext[c].size();
+  }
+  // local ids: own rows below R, halo slots from R, then 32 zero slots (one per bank) after the
+  // longest halo padded to 4
+  int64_t lx_max = 0;
+  for (int c = 0; c < nb; ++c) lx_max = std::max(lx_max, lxp[c]);
+  if (lx_max > 65535) return;  // does not fit 16-bit local ids
+  const int Lp = (int)((lx_max + 3) & ~(int64_t)3);
+  const int zero_id = R + Lp;
+  if (push) {
     for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + lxp[c];
     if (inbox_off[nb] > (int64_t)INT32_MAX) return;  // inbox slots do not fit 32 bits
     // where each run goes in its owner's lists: consumers in order
@@ -466,7 +474,7 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
               sp[q] = (uint16_t)lid[i];
               hs[a + i] = slot + q;
             } else {
-              sp[q] = (uint16_t)(kPadSrc | (-1 - i));
+              sp[q] = (uint16_t)(zero_id + (((-1 - i) - zero_id) & 31));
             }
           }
           slot += L;
@@ -476,7 +484,6 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
       }
     });
   } else {
-    for (int c = 0; c < nb; ++c) lxp[c] = (int64_t)ext[c].size();
     for (int c = 0; c < nb; ++c) inbox_off[c + 1] = inbox_off[c] + ((lxp[c] + 3) & ~(int64_t)3);
   }
 
@@ -613,14 +620,8 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
       P.src = std::move(src);
     }
   });
-  int lx_max = 0;
   size_t blk_max = 0;
-  for (int b = 0; b < nb; ++b) {
-    lx_max = std::max(lx_max, plans[b].H.lx);
-    blk_max = std::max(blk_max, (size_t)plans[b].H.bytes);
-  }
-  const int Lp = (lx_max + 3) & ~3;
-  const int zero_id = R + Lp;  // 32 zero slots from here, one per bank
+  for (int b = 0; b < nb; ++b) blk_max = std::max(blk_max, (size_t)plans[b].H.bytes);
   const size_t floats = (size_t)6 * R + Lp + 32;
   const size_t smem = 4 * floats + blk_max;
   if (zero_id + 31 > 65535 || smem > smem_limit || R > 32767) return;  // does not fit
@@ -685,11 +686,6 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
       // per entry)
       for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = push ? hslot[b][t] : (int32_t)t;
       for (int j = rb; j < re; ++j) extpos[j] = j - rb - R;
-      if (push) {  // the padding of the send list reads the zero slot of the bank it names
-        uint16_t* sp = reinterpret_cast<uint16_t*>(B + H->off_src);
-        for (size_t e = 0; e < plans[b].src.size(); ++e)
-          if (sp[e] >= kPadSrc) sp[e] = (uint16_t)(zero_id + (((sp[e] & 31) - zero_id) & 31));
-      }
       auto lid = [&](int j) -> uint16_t { return (uint16_t)(R + extpos[j]); };
       const int2* meta = reinterpret_cast<const int2*>(B + H->off_meta);
       const short* srow = reinterpret_cast<const short*>(B + H->off_srow);
