@@ -443,10 +443,10 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
         pcount[o] += (len + kSendPiece - 1) / kSendPiece;
       }
     }
-    for (int o = 0; o < nb; ++o) {
+    parallel_items(nb, [&](int o, int) {
       sends[o].src.resize(scount[o]);
       sends[o].pieces.resize(pcount[o]);
-    }
+    });
     // the placement, written straight into the owners' lists (disjoint ranges per consumer)
     parallel_items(nb, [&](int c, int) {
       const std::vector<int32_t>& xc = ext[c];
