@@ -300,10 +300,10 @@ gn_status build_halo(gn_graph* g, const std::vector<int32_t>& rp, const int32_t*
   bool push = want == GN_GATHER_HALO_PUSH ||
               (want == GN_GATHER_HALO && (double)vals < kPullDensity * (double)std::max<int64_t>(sectors, 1));
   HaloBlocks hb;
-  for (int attempt = 0; attempt < 2 && !hb.fits; ++attempt, push = !push) {
-    if (attempt == 1 && want != GN_GATHER_HALO) break;
+  encode_halo_blocks(n, rp, ci, part, ext, push, smem_limit, &hb);
+  if (!hb.fits && want == GN_GATHER_HALO) {  // the automatic choice tries the other exchange
+    push = !push;
     encode_halo_blocks(n, rp, ci, part, ext, push, smem_limit, &hb);
-    if (hb.fits) break;
   }
   if (!hb.fits) return GN_OK;
   GN_CUDA(cudaMalloc(&g->d_hoff, sizeof(int64_t) * (nb + 1)));
@@ -390,8 +390,8 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
   // place_piece.  The owner o sends its runs consumer by consumer: a piece (first inbox slot,
   // length, first source, 0) per kSendPiece slots from each run's start, and the source id of
   // every slot (the owner-local id read, or for padding the zero slot of the bank place_piece
-  // names).  hslot: the inbox slot
-  // (within c's region) of ext[c][t].  Pull: the halo in ext order, 4-slot aligned regions.
+  // names).  hslot: the inbox slot (within c's region) of ext[c][t].  Pull: the halo in ext
+  // order, 4-slot aligned regions.
   struct Sends {
     std::vector<int4> pieces;  // all four fields multiples of 4 (but the last)
     std::vector<uint16_t> src;
@@ -630,10 +630,10 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
   const size_t blob_bytes = (size_t)std::max<int64_t>(hoff[nb], 16);
   std::unique_ptr<unsigned char[]> blob(new unsigned char[blob_bytes]);
 
-  // pass 2, per CTA: the 16-bit local ids (own row r -> r, external halo t -> R + t,
-  // padding -> the zero slot)
+  // pass 2, per CTA: the 16-bit local ids (own row r -> r, external vertex -> R + its halo
+  // slot, padding -> a zero slot)
   struct EncodeScratch {
-    std::unique_ptr<int32_t[]> extpos;  // halo slot of each external id (set before it is read)
+    std::unique_ptr<int32_t[]> extpos;  // local id - R of each vertex the CTA reads (set before it is read)
     std::vector<uint16_t> lids[32];
     std::vector<int> cols[32];
     ColorScratch cs;
