@@ -5,6 +5,9 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#ifdef __linux__
+#include <sched.h>
+#endif
 
 #include <algorithm>
 #include <atomic>
@@ -146,9 +149,19 @@ gn_status copy_out(gn_graph* g, void* dst, const void* dev_src, size_t bytes);
 // blocks are fixed by n and the thread count only, and every caller writes disjoint outputs,
 // so results do not depend on scheduling.  The blocks run on a pool of worker threads started
 // once per process (run_parts, gn_graph.cu): a block costs a wake-up, not a thread start.
+// The thread count is the CPUs this process may run on (its affinity mask, which a container's
+// CPU set limits), else the hardware's count; at most 64.
 inline int host_threads() {
-  const unsigned h = std::thread::hardware_concurrency();
-  return (int)std::max(1u, std::min(h == 0 ? 1u : h, 64u));
+  static const int count = [] {
+    unsigned h = std::thread::hardware_concurrency();
+#ifdef __linux__
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    if (sched_getaffinity(0, sizeof set, &set) == 0 && CPU_COUNT(&set) > 0) h = (unsigned)CPU_COUNT(&set);
+#endif
+    return (int)std::max(1u, std::min(h == 0 ? 1u : h, 64u));
+  }();
+  return count;
 }
 // runs f(0) .. f(parts - 1), parts <= host_threads(), concurrently; returns when all are done
 void run_parts(int parts, const std::function<void(int)>& f);
