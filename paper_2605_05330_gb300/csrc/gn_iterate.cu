@@ -225,11 +225,26 @@ gn_status configure_partition(gn_graph* g, const std::vector<int32_t>& rp, const
   // Entries of rows above kHeavyRowCost entries count twice: they are summed by whole warps
   // from randomly placed neighbours (no bank-aware layout), at about half the rate.
   const int64_t alpha = 4;
-  std::vector<int64_t> C((size_t)n + 1, 0);
-  for (int i = 0; i < n; ++i) {
+  auto cost = [&](int i) {
     const int64_t d = rp[i + 1] - rp[i];
-    C[i + 1] = C[i] + d + (d > kHeavyRowCost ? d : 0) + alpha;
-  }
+    return d + (d > kHeavyRowCost ? d : 0) + alpha;
+  };
+  // the prefix C in two passes over the same row blocks on the host threads: each block's sum,
+  // then each block's prefix from its offset
+  std::unique_ptr<int64_t[]> C(new int64_t[(size_t)n + 1]);
+  std::vector<int64_t> boff(host_threads() + 1, 0);
+  constexpr int kRowGrain = 16384;
+  parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
+    int64_t sum = 0;
+    for (int i = lo; i < hi; ++i) sum += cost(i);
+    boff[t + 1] = sum;
+  });
+  for (size_t t = 1; t < boff.size(); ++t) boff[t] += boff[t - 1];
+  C[0] = 0;
+  parallel_for(n, kRowGrain, [&](int lo, int hi, int t) {
+    int64_t at = boff[t];
+    for (int i = lo; i < hi; ++i) C[i + 1] = at += cost(i);
+  });
   const int64_t total = C[n];
   (void)nnz;
   int nb = (int)std::min<int64_t>(g->num_sms, std::max<int64_t>(1, (total + 2047) / 2048));
