@@ -338,13 +338,24 @@ static void halo_lists(int n, const std::vector<int32_t>& rp, const int32_t* ci,
     if (bits.empty()) bits.assign((size_t)n / 64 + 1, 0);
     {
       const int rb = part[b], re = part[b + 1];
+      // every entry marked (no branch per entry), then the CTA's own rows unmarked
       int wlo = INT32_MAX, whi = -1;
       for (int64_t e = rp[rb]; e < rp[re]; ++e) {
         const int j = ci[e];
-        if (j >= rb && j < re) continue;
         bits[j >> 6] |= 1ull << (j & 63);
         wlo = std::min(wlo, j >> 6);
         whi = std::max(whi, j >> 6);
+      }
+      if (re > rb) {
+        const int w0 = rb >> 6, w1 = (re - 1) >> 6;
+        const uint64_t lo = ~0ull << (rb & 63), hi = ~0ull >> (63 - ((re - 1) & 63));
+        if (w0 == w1) {
+          bits[w0] &= ~(lo & hi);
+        } else {
+          bits[w0] &= ~lo;
+          for (int wd = w0 + 1; wd < w1; ++wd) bits[wd] = 0;
+          bits[w1] &= ~hi;
+        }
       }
       std::vector<int32_t>& xb = ext[b];
       size_t count = 0;
