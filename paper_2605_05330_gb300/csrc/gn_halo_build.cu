@@ -527,8 +527,8 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
           heavy.push_back(r);
           continue;
         }
-        bool bnd = false;
-        for (int64_t e = a; e < c && !bnd; ++e) bnd = (ci[e] < rb || ci[e] >= re);
+        // a row's entries are increasing, so it reads another CTA's row iff its first or last does
+        const bool bnd = c > a && (ci[a] < rb || ci[c - 1] >= re);
         (bnd ? light_bnd : light_int).push_back(r);
       }
       // by degree, descending, then by row (the lists are in row order and light degrees are at
