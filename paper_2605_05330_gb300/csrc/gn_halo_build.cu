@@ -644,7 +644,7 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
   // pass 2, per CTA: the 16-bit local ids (own row r -> r, external vertex -> R + its halo
   // slot, padding -> a zero slot)
   struct EncodeScratch {
-    std::unique_ptr<int32_t[]> extpos;  // local id - R of each vertex the CTA reads (set before it is read)
+    std::unique_ptr<uint16_t[]> lidtab;  // local id of each vertex the CTA reads (set before it is read)
     std::vector<uint16_t> lids[32];
     std::vector<int> cols[32];
     ColorScratch cs;
@@ -661,8 +661,8 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
   for (EncodeScratch& X : scratch) memset(X.extra, 0, sizeof X.extra);
   parallel_items(nb, [&](int b, int t) {
     EncodeScratch& X = scratch[t];
-    if (!X.extpos) X.extpos.reset(new int32_t[std::max(n, 1)]);
-    int32_t* extpos = X.extpos.get();
+    if (!X.lidtab) X.lidtab.reset(new uint16_t[std::max(n, 1)]);
+    uint16_t* lidtab = X.lidtab.get();
     std::vector<uint16_t>* lids = X.lids;
     std::vector<int>* cols = X.cols;
     ColorScratch& cs = X.cs;
@@ -693,11 +693,12 @@ static void encode_halo_blocks(int n, const std::vector<int32_t>& rp, const int3
       }
       HaloHeader* H = reinterpret_cast<HaloHeader*>(B);
       H->zero_id = zero_id;
-      // a vertex's local id is R + extpos[j]: halo slots from R up, own rows below (no branch
-      // per entry)
-      for (size_t t = 0; t < ext[b].size(); ++t) extpos[ext[b][t]] = push ? hslot[b][t] : (int32_t)t;
-      for (int j = rb; j < re; ++j) extpos[j] = j - rb - R;
-      auto lid = [&](int j) -> uint16_t { return (uint16_t)(R + extpos[j]); };
+      // a vertex's local id is one table read (own rows below R, halo slots from R; no branch
+      // per entry; every id fits 16 bits, zero_id + 31 <= 65535 was checked)
+      for (size_t t = 0; t < ext[b].size(); ++t)
+        lidtab[ext[b][t]] = (uint16_t)(R + (push ? hslot[b][t] : (int32_t)t));
+      for (int j = rb; j < re; ++j) lidtab[j] = (uint16_t)(j - rb);
+      auto lid = [&](int j) -> uint16_t { return lidtab[j]; };
       const int2* meta = reinterpret_cast<const int2*>(B + H->off_meta);
       const short* srow = reinterpret_cast<const short*>(B + H->off_srow);
       uint16_t* sell = reinterpret_cast<uint16_t*>(B + H->off_sell);
