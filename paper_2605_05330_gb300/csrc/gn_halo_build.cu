@@ -152,13 +152,25 @@ static void color_slice64(int W, const uint16_t (*lid)[64], const int* nl, uint8
       cs.at_b[cs.ebank[f] * W + x] = (int16_t)f;
     }
   };
+  // Lane l's colour set stays in a register while its entries are coloured: an alternating
+  // path reaches lanes only through edges of colour a, which is free at l, so it never changes
+  // lane l's set.
   int e = 0;
   for (int l = 0; l < 32; ++l) {
+    uint64_t lu = 0;
     for (int k = 0; k < nl[l]; ++k, ++e) {
       const int b = lid[l][k] & 31;
       cs.elane[e] = (uint8_t)l;
       cs.ebank[e] = (uint8_t)b;
-      const uint64_t both = ~(ul[l] | ub[b]) & mask;
+      const uint64_t both = ~(lu | ub[b]) & mask;
+      if (both && !tables) {  // the lowest colour free at both ends
+        const uint64_t bit = both & (0 - both);
+        lu |= bit;
+        ub[b] |= bit;
+        cs.ecol[e] = (uint8_t)__builtin_ctzll(bit);
+        continue;
+      }
+      ul[l] = lu;
       int a;
       if (both) {
         a = __builtin_ctzll(both);
@@ -196,7 +208,9 @@ static void color_slice64(int W, const uint16_t (*lid)[64], const int* nl, uint8
         }
       }
       put(e, a);
+      lu = ul[l];
     }
+    ul[l] = lu;
   }
   e = 0;
   for (int l = 0; l < 32; ++l)
