@@ -325,6 +325,26 @@ static void check_blocks(const char* name, int n, const std::vector<int32_t>& rp
   CHECK(halo_ok, name);
 }
 
+// A graph whose first slice needs more than 64 colours: CTA 0's rows 0..31 each read the 64
+// even-ranked vertices of 128 in CTA 1 and rows 32..63 the odd-ranked ones, so CTA 0's halo holds
+// all 128 and the first slice's 2048 entries fall on 16 banks, 128 on each.
+static void crowded_graph(int n, std::vector<int32_t>& rp, std::vector<int32_t>& ci) {
+  std::vector<std::vector<int32_t>> adj(n);
+  const int base = n / 2 + 5;
+  for (int r = 0; r < 64; ++r)
+    for (int t = r < 32 ? 0 : 1; t < 128; t += 2) {
+      adj[r].push_back(base + t);
+      adj[base + t].push_back(r);
+    }
+  rp.assign(n + 1, 0);
+  ci.clear();
+  for (int i = 0; i < n; ++i) {
+    std::sort(adj[i].begin(), adj[i].end());
+    ci.insert(ci.end(), adj[i].begin(), adj[i].end());
+    rp[i + 1] = (int32_t)ci.size();
+  }
+}
+
 static void check_all_blocks(std::mt19937& rng) {
   std::vector<int32_t> rp, ci;
   random_graph(rng, 9000, 6, 40, 4, rp, ci);  // local, with hubs: interior slices, dense halos
@@ -336,6 +356,9 @@ static void check_all_blocks(std::mt19937& rng) {
   random_graph(rng, 300, 3, 5, 0, rp, ci);  // one slice per CTA, ragged
   check_blocks("blocks, small graph, push", 300, rp, ci, 3, true);
   check_blocks("blocks, small graph, pull", 300, rp, ci, 3, false);
+  crowded_graph(600, rp, ci);  // more than 64 colours in a slice, folded past the width
+  check_blocks("blocks, crowded banks, pull", 600, rp, ci, 2, false);
+  check_blocks("blocks, crowded banks, push", 600, rp, ci, 2, true);
 }
 
 int main() {
