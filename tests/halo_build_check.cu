@@ -356,6 +356,17 @@ static void check_all_blocks(std::mt19937& rng) {
   random_graph(rng, 300, 3, 5, 0, rp, ci);  // one slice per CTA, ragged
   check_blocks("blocks, small graph, push", 300, rp, ci, 3, true);
   check_blocks("blocks, small graph, pull", 300, rp, ci, 3, false);
+  {  // a shared-memory limit no block fits: nothing is built
+    std::vector<int32_t> part = {0, 150, 300};
+    std::vector<std::vector<int32_t>> ext(2);
+    int64_t vals = 0, sectors = 0;
+    gn::halo_lists(300, rp, ci.data(), part, ext, &vals, &sectors);
+    for (bool push : {false, true}) {
+      gn::HaloBlocks hb;
+      gn::encode_halo_blocks(300, rp, ci.data(), part, ext, push, 1024, &hb);
+      CHECK(!hb.fits && !hb.blob, "blocks over the shared-memory limit are not built");
+    }
+  }
   crowded_graph(600, rp, ci);  // more than 64 colours in a slice, folded past the width
   check_blocks("blocks, crowded banks, pull", 600, rp, ci, 2, false);
   check_blocks("blocks, crowded banks, push", 600, rp, ci, 2, true);
